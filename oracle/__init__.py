@@ -1,0 +1,125 @@
+"""FP64 CPU oracle for sparse GEE -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, the smoke check in ``__graft_entry__.py`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library under ``paper_2406_03726_gb300``
+never imports it, and it imports nothing from the library.
+
+Two independent forms of the same definitions:
+
+* ``embed`` / ``csr`` / ``degrees`` / ``label_counts`` / ``class_counts`` call the plain C
+  edge-list oracle in ``gee_oracle.c`` (Section 2 edge-list GEE, Section 3 CSR).
+* ``dense.embed_dense`` evaluates Table 1 literally with dense NumPy matrices (small N).
+
+Parity pinning: every function here is checked in ``tests/test_oracle.py`` against
+closed forms, invariants, a library stable sort, brute force on tiny inputs and the
+CSR example of Section 3 -- never against the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import build_oracle, library_path
+
+DIAG_AUG = 1
+LAPLACIAN = 2
+CORRELATION = 4
+ALL_OPTIONS = DIAG_AUG | LAPLACIAN | CORRELATION
+
+ERR_INDEX = 1
+ERR_LABEL = 2
+ERR_WEIGHT = 4
+ERR_ARG = 8
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = library_path()
+        src = os.path.join(os.path.dirname(__file__), "gee_oracle.c")
+        if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src):
+            build_oracle()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        lib.oracle_validate.argtypes = [P, P, P, i64, i32, P, i32, u32]
+        lib.oracle_validate.restype = ctypes.c_int
+        lib.oracle_label_counts.argtypes = [P, i32, i32, P]
+        lib.oracle_label_counts.restype = None
+        lib.oracle_csr.argtypes = [P, P, P, i64, i32, P, P, P]
+        lib.oracle_csr.restype = None
+        lib.oracle_degrees.argtypes = [P, P, i64, i32, u32, P]
+        lib.oracle_degrees.restype = None
+        lib.oracle_class_counts.argtypes = [P, P, i64, i32, P, i32, P]
+        lib.oracle_class_counts.restype = None
+        lib.oracle_embed.argtypes = [P, P, P, i64, i32, P, i32, u32, P]
+        lib.oracle_embed.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def validate(src, dst, w, N, labels, K, flags=0) -> int:
+    src, dst, w, y = _i32(src), _i32(dst), _f32(w), _i32(labels)
+    return _load().oracle_validate(_ptr(src), _ptr(dst), _ptr(w), src.size, N, _ptr(y), K, flags)
+
+
+def label_counts(labels, K) -> np.ndarray:
+    y = _i32(labels)
+    nk = np.zeros(K, np.int64)
+    _load().oracle_label_counts(_ptr(y), y.size, K, _ptr(nk))
+    return nk
+
+
+def csr(src, dst, w, N):
+    """(rowptr int64 [N+1], col int32 [E], val float32 [E]) -- stable by input order."""
+    src, dst, w = _i32(src), _i32(dst), _f32(w)
+    E = src.size
+    rowptr = np.zeros(N + 1, np.int64)
+    col = np.zeros(E, np.int32)
+    val = np.zeros(E, np.float32)
+    _load().oracle_csr(_ptr(src), _ptr(dst), _ptr(w), E, N, _ptr(rowptr), _ptr(col), _ptr(val))
+    return rowptr, col, val
+
+
+def degrees(src, w, N, flags=0) -> np.ndarray:
+    src, w = _i32(src), _f32(w)
+    deg = np.zeros(N, np.float64)
+    _load().oracle_degrees(_ptr(src), _ptr(w), src.size, N, flags, _ptr(deg))
+    return deg
+
+
+def class_counts(src, dst, N, labels, K) -> np.ndarray:
+    src, dst, y = _i32(src), _i32(dst), _i32(labels)
+    C = np.zeros((N, K), np.int64)
+    _load().oracle_class_counts(_ptr(src), _ptr(dst), src.size, N, _ptr(y), K, _ptr(C))
+    return C
+
+
+def embed(src, dst, w, N, labels, K, flags=0) -> np.ndarray:
+    """Z (N x K, float64).  Raises ValueError with the error bits on invalid input."""
+    src, dst, w, y = _i32(src), _i32(dst), _f32(w), _i32(labels)
+    Z = np.zeros((N, K), np.float64)
+    err = _load().oracle_embed(_ptr(src), _ptr(dst), _ptr(w), src.size, N, _ptr(y), K, flags, _ptr(Z))
+    if err:
+        raise ValueError(f"oracle: invalid input (error bits {err})")
+    return Z
+
+
+def embed_graph(g, flags=0) -> np.ndarray:
+    return embed(g.src, g.dst, g.w, g.N, g.labels, g.K, flags)
