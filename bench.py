@@ -1,0 +1,349 @@
+"""Benchmark of the sparse GEE hot path on GB300.
+
+One step = one full embedding (all options on) of the workload graph through the C ABI:
+label counts and checks, CSR build (radix sort by source), degrees and node table,
+label-gather product with the fused epilogue.  Inputs are resident in HBM; L2 is flushed
+(256 MiB write) before every timed step, outside the timed interval.
+
+Prints ONE JSON line (rank 0).  Keys follow the driver's contract; `roofline` describes
+the dominant kernel (per-kernel CUDA-event times from gee_embed_timed over the timed
+steps), `cpu_baseline` times the FP64 oracle on this host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sbm10k|sbm2k|cl600k]
+  python bench.py --impl reference ...     (the oracle arm)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GEE edges/s and % HBM roofline (all options on); p50/p99 served latency"
+UNIT = "edges/s"
+ALL_OPTIONS = 7
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "sbm10k": dict(desc="SBM N=10,000, K=3, priors [0.2,0.3,0.5], p_in 0.13, p_out 0.10 "
+                        "(~5.56M undirected edges, both directions stored), fp32 weights U(0,1], "
+                        "all options (diag-aug + Laplacian + correlation), seed 2"),
+    "sbm2k": dict(desc="SBM N=2,000, K=3, priors [0.2,0.3,0.5], p_in 0.13, p_out 0.10, unweighted, "
+                       "all options, seed 1"),
+    "cl600k": dict(desc="Chung-Lu N=600,000, 10M undirected edges (deduplicated), gamma 2.1, K=50 Zipf(1.2) "
+                        "classes, unweighted, all options, seed 3"),
+}
+
+
+def make_graph(name, rank=0):
+    from synth import chung_lu, sbm
+    if name == "sbm10k":
+        return sbm(10_000, seed=2 + 1000 * rank, weighted=True)
+    if name == "sbm2k":
+        return sbm(2_000, seed=1 + 1000 * rank)
+    if name == "cl600k":
+        return chung_lu(600_000, 10_000_000, seed=3 + 1000 * rank)
+    raise ValueError(name)
+
+
+# ---- algorithmic bytes per launch of each kernel ("Roofline") ------------
+
+def kernel_bytes(g):
+    E, N, K = g.E, g.N, g.K
+    wt = 1 if g.w is not None else 0
+    two = (N - 1).bit_length() > 11
+    b = {}
+    b["k_prep"] = 4 * E + 4 * N
+    if two:
+        b["k_sort_first"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)      # read COO, write packed
+        b["k_sort_final"] = E * (4 + 4 * wt) + E * (4 + 4 * wt)      # read packed, write CSR
+    else:
+        b["k_sort_final"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)      # read COO, write CSR
+    b["k_rowscan"] = 4 * N + 4 * (N + 1) + (0 if wt else 4 * N + 16 * N)
+    b["k_wdeg"] = 4 * E + 4 * (N + 1) + 4 * N + 16 * N if wt else 0
+    b["k_spmm"] = E * (4 + 4 * wt) + 4 * (N + 1) + 8 * N + 4 * N + 4 * N * K
+    return b
+
+
+# ---- helpers ----------------------------------------------------------------------------
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, f in enumerate(fl) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_oracle(g, budget_s=12.0, max_calls=30):
+    import oracle
+    oracle.embed_graph(g, ALL_OPTIONS)  # warm (page-in, build)
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < max_calls and (not times or time.perf_counter() < t_end):
+        t0 = time.perf_counter()
+        oracle.embed_graph(g, ALL_OPTIONS)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+# ---- arms -------------------------------------------------------------------------------
+
+def reference_arm(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    g = make_graph(args.workload)
+    import oracle
+    for _ in range(args.warmup):
+        oracle.embed_graph(g, ALL_OPTIONS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.embed_graph(g, ALL_OPTIONS)
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    v = g.E / mean
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "N": g.N, "E": g.E, "K": g.K},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"full graph per step ({g.E} directed edges), single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def gpu_arm(args):
+    import torch
+    import paper_2406_03726_gb300 as gee
+
+    ws_n, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws_n > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    g = make_graph(args.workload, rank)
+    E, N, K = g.E, g.N, g.K
+    t = lambda a: None if a is None else torch.from_numpy(a).to(dev)
+    src, dst, w, y = t(g.src), t(g.dst), t(g.w), t(g.labels)
+    opts = gee.make_opts(ALL_OPTIONS)
+    nbytes = gee.gee_workspace_size(E, N, K, w is not None, opts)
+    wsb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    Z = torch.empty((N, K), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    phase = np.zeros(gee_phase_count(), np.float32)
+
+    def step_plain():
+        rc = gee.gee_embed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+
+    for _ in range(max(args.warmup, 3)):
+        step_plain()
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())}")
+
+    # ---- timed region: K steps, each bracketed by CUDA events on the launch stream
+    phase_sum = np.zeros_like(phase)
+    phase_cnt = np.zeros_like(phase)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws_n > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))               # L2 flush, outside the timed interval
+            ev[i][0].record(stream)
+            rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
+            ev[i][1].record(stream)
+            if rc:
+                raise RuntimeError(gee.gee_strerror(rc))
+            ok = phase >= 0
+            phase_sum[ok] += phase[ok]
+            phase_cnt[ok] += 1
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws_n > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())}")
+    ms_per_step = total_ms / args.steps
+    value = E * ws_n / (ms_per_step * 1e-3)
+
+    # ---- per-kernel roofline of the dominant kernel
+    names = gee.PHASES
+    avg = {names[i]: float(phase_sum[i] / phase_cnt[i]) for i in range(len(names)) if phase_cnt[i] > 0}
+    kb = kernel_bytes(g)
+    kernels = {k: v for k, v in avg.items() if k in kb and kb[k] > 0}
+    dom = max(kernels, key=lambda k: kernels[k])
+    peaks = load_peaks()
+    achieved = kb[dom] / (kernels[dom] * 1e-3) / 1e9
+    per_kernel = {k: {"ms": round(float(v), 5), "alg_bytes": int(kb[k]),
+                      "gbs": round(kb[k] / (v * 1e-3) / 1e9, 1),
+                      "frac": round(kb[k] / (v * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)}
+                  for k, v in kernels.items()}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_source": peaks["source"], "traffic": traffic_for(dom, args.workload),
+                "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel}
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = e2e_measure(gee, g, dev, stream, opts, args)
+
+    launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "N": N, "E": E, "K": K,
+                       "l2": "flushed before every step (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{ws_n} (independent graphs, no collective)"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "clocks": clk.summary()}
+    if rank == 0:
+        if ws_n == 1 and not args.no_cpu_baseline:
+            times = time_oracle(g)
+            line["cpu_baseline"] = {"value": E / (sum(times) / len(times)), "unit": UNIT, "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"{len(times)} full-graph oracle calls ({E} directed edges each), "
+                                              f"{sum(times):.1f} s, single thread"}
+        print(json.dumps(line))
+    if ws_n > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def gee_phase_count():
+    return 8
+
+
+def e2e_measure(gee, g, dev, stream, opts, args):
+    import torch
+    E, N, K = g.E, g.N, g.K
+    n = gee.gee_host_workspace_size(E, N, K, g.w is not None, opts)
+    wsb = torch.empty(n, dtype=torch.uint8, device=dev)
+    pin = lambda a: None if a is None else torch.from_numpy(a).pin_memory()
+    src, dst, w, y = pin(g.src), pin(g.dst), pin(g.w), pin(g.labels)
+    Z = torch.empty((N, K), dtype=torch.float32).pin_memory()
+    st = np.zeros(1, np.uint32)
+
+    def call():
+        rc = gee.gee_embed_host(src, dst, w, E, N, y, K, opts, Z, wsb, n, stream, st)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+
+    for _ in range(3):
+        call()
+    steps = max(3, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        call()                      # synchronous: returns with Z in host memory
+    dt = (time.perf_counter() - t0) / steps
+    h2d = 8 * E + (4 * E if g.w is not None else 0) + 4 * N
+    d2h = 4 * N * K + 4
+    return {"value": E / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "host_memory": "pinned"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one matches."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        return d.get(workload, {}).get(kernel)
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gee", choices=["gee", "reference"])
+    ap.add_argument("--workload", default="sbm10k", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

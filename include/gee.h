@@ -1,0 +1,177 @@
+/*
+ * gee.h -- C ABI of the GB300 sparse Graph Encoder Embedding library (libgee.so).
+ *
+ * Method: Qin & Shen, "Efficient Graph Encoder Embedding for Large Sparse Graphs in
+ * Python".  For a graph with N nodes, a directed edge list (i, j, e_ij) and labels
+ * y_j in {0..K-1} (or -1 = unlabelled), the library computes the N x K embedding
+ *
+ *     Z = A W                                              (Section 2, Eq. 1)
+ *     Z_i^k = sum_{j : y_j = k} e_ij / n_k                 (Section 2, per-entry form)
+ *
+ * where W_j = e_{y_j} / n_{y_j} is the normalised one-hot label matrix and n_k the class
+ * size, with the three options of Section 2 / Table 1:
+ *     GEE_DIAG_AUG     A -> A + I
+ *     GEE_LAPLACIAN    A -> D^-1/2 A D^-1/2, D = diag(row sums), taken after A + I
+ *     GEE_CORRELATION  Z_i -> Z_i / ||Z_i||_2 (rows with norm 0 stay 0)
+ * The sparse matrices are held in CSR (Section 3) built on the device.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or documented "device" are device pointers (cudaMalloc / torch
+ *     CUDA tensors) on the current device; the caller owns them.  The library allocates
+ *     nothing: all scratch lives in the caller's workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Device
+ *     work is enqueued on it and the call returns without synchronising unless stated.
+ *   - Return value: GEE_OK or a gee_error code for problems visible on the host (bad
+ *     arguments, sizes, workspace, CUDA launch errors).  Problems that depend on the
+ *     data (an id out of range, a bad label or weight) are reported as GEE_STATUS_* bits
+ *     in a device word (`d_status`) once the stream reaches that point; outputs are then
+ *     undefined but every memory access stays inside the caller's buffers.
+ *   - Layouts: src/dst/labels int32, w float32, Z float32 row-major [N][K].
+ *   - Limits: 0 <= N <= 2^21, 0 <= E < 2^30, 1 <= K <= 64.
+ */
+#ifndef GEE_H
+#define GEE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Embedding options (Section 2, Table 1). */
+#define GEE_DIAG_AUG 1u
+#define GEE_LAPLACIAN 2u
+#define GEE_CORRELATION 4u
+#define GEE_ALL_OPTIONS 7u
+
+/* Supported sizes. */
+#define GEE_MAX_N (1 << 21)
+#define GEE_MAX_E ((int64_t)1 << 30)
+#define GEE_MAX_K 64
+
+/* Host-visible return codes. */
+typedef enum gee_error {
+    GEE_OK = 0,
+    GEE_ERR_ARG = 1,       /* a NULL pointer where one is required, negative size, ... */
+    GEE_ERR_TOO_LARGE = 2, /* N, E or K beyond the limits above */
+    GEE_ERR_WORKSPACE = 3, /* workspace NULL, too small, or not 256-byte aligned */
+    GEE_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+    GEE_ERR_DATA = 5       /* (blocking calls only) the device reported GEE_STATUS_* bits */
+} gee_error;
+
+/* Device status bits, OR-ed into the status word of a call. */
+#define GEE_STATUS_INDEX 1u   /* an edge endpoint outside [0, N) */
+#define GEE_STATUS_LABEL 2u   /* a label outside [-1, K) */
+#define GEE_STATUS_WEIGHT 4u  /* a non-finite weight, or a negative one with GEE_LAPLACIAN */
+#define GEE_STATUS_TIMEOUT 8u /* a bounded inter-CTA wait gave up (should never happen) */
+
+/* Options.  Zero-initialise and set `flags`; the tuning fields select the kernel
+ * shapes (0 = automatic) and never change which value is computed, only the order of
+ * floating-point additions. */
+typedef struct gee_opts {
+    uint32_t flags;        /* GEE_DIAG_AUG | GEE_LAPLACIAN | GEE_CORRELATION */
+    int32_t hub_threshold; /* rows with more entries are split into chunks of this many
+                              entries across CTAs and merged; 0 = automatic */
+    int32_t lanes_per_row; /* threads cooperating on one light row: 1,2,4,...,32; 0 = auto */
+    int32_t reserved;      /* must be 0 */
+} gee_opts;
+
+/* Bytes of device workspace gee_embed needs for a graph of this size.  `weighted` is
+ * non-zero when a weight array will be passed.  opts may be NULL (defaults). */
+size_t gee_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts);
+
+/*
+ * gee_embed -- Z = A W with the selected options (Eq. 1, Table 1), from an edge list.
+ *
+ *   d_src, d_dst  device int32 [E]: edge (d_src[e], d_dst[e]) adds its weight to
+ *                 A[src][dst] only (store both directions for an undirected graph);
+ *                 duplicates add up.  May be NULL when E == 0.
+ *   d_w           device float32 [E] edge weights e_ij, or NULL for weight 1 (Section 2).
+ *   E, N          edge and node counts.
+ *   d_labels      device int32 [N], y_j in [0, K) or -1 (unlabelled: in no class, still
+ *                 gets a row of Z).
+ *   K             number of classes.
+ *   opts          flags and tuning; NULL = no options, automatic tuning.
+ *   d_Z           device float32 [N][K], fully written.
+ *   d_workspace   device scratch of at least gee_workspace_size(...) bytes, 256-byte
+ *                 aligned; its contents on entry are ignored.  Calls that run
+ *                 concurrently need separate workspaces.
+ *   stream        cudaStream_t (void*).
+ *   d_status      device uint32, or NULL: receives the GEE_STATUS_* bits of this call
+ *                 (0 = success) when the stream reaches the end of the call.
+ *
+ * Steps (all on the device, stream-ordered): label counts n_k and input checks; CSR of
+ * A by a stable LSD radix sort on the source id (rows keep input order, Section 3);
+ * degrees D (after A + I) and the node table s_j = D_jj^-1/2 / n_{y_j}; the label-gather
+ * product with the augmentation term, the D_ii^-1/2 scaling and the row 2-norm fused
+ * into its epilogue.  Deterministic: the same input gives bit-identical Z.
+ */
+int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+              const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
+              void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status);
+
+/*
+ * gee_embed_timed -- gee_embed with CUDA events recorded on `stream` between its launch
+ * phases; waits for the stream and stores the device time of each phase, in
+ * milliseconds, into the HOST array phase_ms[GEE_NUM_PHASES] (-1 for a phase that
+ * launched nothing).  For measurement only: the work and the result are those of
+ * gee_embed.  Phases, in launch order:
+ *   0 workspace memset, 1 k_prep (label counts, checks, digit histograms),
+ *   2 k_sort first pass (2-pass graphs), 3 k_sort final pass (writes the CSR),
+ *   4 k_rowscan (index_pointers, unweighted degrees), 5 k_hubprep (hub-row chunks),
+ *   6 k_wdeg (weighted degrees), 7 k_spmm (Z with the fused epilogue).
+ */
+#define GEE_NUM_PHASES 8
+int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                    const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
+                    void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status,
+                    float *phase_ms);
+
+/*
+ * gee_build_csr -- the sparse matrices gee_embed builds, copied out for inspection
+ * (Section 3 CSR; Section 2 n_k and D).  Same inputs and workspace as gee_embed.
+ *
+ *   d_rowptr  device int32 [N+1]  index_pointers of A (rowptr[N] = E)
+ *   d_col     device int32 [E]    col_indices, rows in input order
+ *   d_val     device float32 [E]  data (1.0 for unweighted input), or NULL to skip
+ *   d_nk      device int32 [K]    class sizes n_k, or NULL
+ *   d_deg     device float32 [N]  D_ii (row sum, +1 with GEE_DIAG_AUG), or NULL
+ * Integer outputs are exact; for unweighted input d_deg holds exact integers.
+ */
+int gee_build_csr(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                  const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_rowptr,
+                  int32_t *d_col, float *d_val, int32_t *d_nk, float *d_deg, void *d_workspace,
+                  size_t workspace_bytes, void *stream, uint32_t *d_status);
+
+/*
+ * gee_class_counts -- per-class neighbour counts C[i][k] = #{entries j of row i with
+ * y_j = k} from a CSR (Section 2: Z_i^k n_k for unweighted input without options).
+ * d_rowptr [N+1], d_col [nnz], d_labels [N] device int32; d_C device int32 [N][K].
+ * Exact integer arithmetic.  Labels outside [0, K) are ignored.
+ */
+int gee_class_counts(const int32_t *d_rowptr, const int32_t *d_col, int32_t N, const int32_t *d_labels,
+                     int32_t K, int32_t *d_C, void *stream);
+
+/*
+ * gee_embed_host -- gee_embed on HOST buffers (pinned memory gives full copy speed):
+ * copies src/dst/w/labels to the device workspace, embeds, copies Z back and waits for
+ * the stream.  Returns GEE_ERR_DATA (and stores the bits in *status if non-NULL) when
+ * the device reported bad data.  Workspace: gee_host_workspace_size(...) bytes.
+ */
+size_t gee_host_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts);
+int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
+                   const int32_t *labels, int32_t K, const gee_opts *opts, float *Z,
+                   void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *status);
+
+/* Human-readable text of a gee_error code. */
+const char *gee_strerror(int code);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int gee_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEE_H */

@@ -1,0 +1,101 @@
+"""GB300-native sparse Graph Encoder Embedding (Qin & Shen, arXiv 2406.03726).
+
+``Z = A W`` (Eq. 1) with diagonal augmentation, Laplacian normalisation and correlation
+(Section 2, Table 1), computed by hand-written sm_103a CUDA kernels behind the C ABI of
+``include/gee.h``.  ``_native`` holds the one-to-one ctypes binding; the helpers below
+only allocate device memory with PyTorch and call it.
+"""
+from __future__ import annotations
+
+from ._native import (  # noqa: F401
+    gee_build_csr,
+    gee_class_counts,
+    gee_embed,
+    gee_embed_host,
+    gee_embed_timed,
+    gee_host_workspace_size,
+    gee_opts,
+    gee_strerror,
+    gee_version,
+    gee_workspace_size,
+    lib,
+    make_opts,
+)
+
+DIAG_AUG = 1
+LAPLACIAN = 2
+CORRELATION = 4
+ALL_OPTIONS = 7
+
+STATUS_INDEX = 1
+STATUS_LABEL = 2
+STATUS_WEIGHT = 4
+STATUS_TIMEOUT = 8
+
+PHASES = ("memset", "k_prep", "k_sort_first", "k_sort_final", "k_rowscan", "k_hubprep", "k_wdeg",
+          "k_spmm")
+
+MAX_N = 1 << 21
+MAX_E = 1 << 30
+MAX_K = 64
+
+
+class GeeError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__(f"{what}: {gee_strerror(code)} (code {code})" if what else gee_strerror(code))
+        self.code = code
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise GeeError(rc, what)
+
+
+def workspace(E, N, K, weighted, opts=None, device=None):
+    """A device byte tensor large enough for ``gee_embed`` on this shape."""
+    import torch
+    n = gee_workspace_size(E, N, K, weighted, opts)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def embed(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, ws=None, Z=None,
+          status=None, stream=None):
+    """Z (float32 [N, K], on the device of ``src``) from device tensors.  ``status`` may be a
+    uint32 device tensor of one element receiving the GEE_STATUS_* bits."""
+    import torch
+    E = int(src.numel())
+    opts = make_opts(flags, hub_threshold, lanes_per_row)
+    dev = labels.device
+    if Z is None:
+        Z = torch.empty((N, K), dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = workspace(E, N, K, w is not None, opts, dev)
+    rc = gee_embed(src, dst, w, E, N, labels, K, opts, Z, ws, ws.numel(), stream, status)
+    _check(rc, "gee_embed")
+    return Z
+
+
+def build_csr(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, status=None, stream=None):
+    """(rowptr int32 [N+1], col int32 [E], val float32 [E], n_k int32 [K], deg float32 [N])."""
+    import torch
+    E = int(src.numel())
+    dev = labels.device
+    opts = make_opts(flags, hub_threshold, lanes_per_row)
+    n = gee_workspace_size(E, N, K, w is not None, opts)
+    ws = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    rowptr = torch.empty(N + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(E, dtype=torch.int32, device=dev)
+    val = torch.empty(E, dtype=torch.float32, device=dev)
+    nk = torch.empty(K, dtype=torch.int32, device=dev)
+    deg = torch.empty(N, dtype=torch.float32, device=dev)
+    rc = gee_build_csr(src, dst, w, E, N, labels, K, opts, rowptr, col, val, nk, deg, ws, ws.numel(), stream,
+                       status)
+    _check(rc, "gee_build_csr")
+    return rowptr, col, val, nk, deg
+
+
+def class_counts(rowptr, col, N, labels, K, stream=None):
+    import torch
+    C = torch.empty((N, K), dtype=torch.int32, device=labels.device)
+    _check(gee_class_counts(rowptr, col, N, labels, K, C, stream), "gee_class_counts")
+    return C

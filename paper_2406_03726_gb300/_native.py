@@ -1,0 +1,140 @@
+"""ctypes binding of libgee.so: one Python function per C entry point, same names, same
+arguments.  Arguments are marshalled only (tensors / ints -> pointers); every step of
+the computation runs in the CUDA library.  There is no fallback: if the library is not
+built, every call raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB_PATH
+
+_P = ctypes.c_void_p
+_I32, _I64, _U32, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+
+
+class gee_opts(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("hub_threshold", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_SIGNATURES = {
+    "gee_version": ([], ctypes.c_int),
+    "gee_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "gee_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_host_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_embed": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
+    "gee_embed_timed": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P, _P], ctypes.c_int),
+    "gee_build_csr": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
+                      ctypes.c_int),
+    "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
+    "gee_embed_host": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib():
+    """The loaded libgee.so.  Raises RuntimeError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgee.so is not built ({LIB_PATH}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def ptr(x):
+    """Device/host address of a tensor, ndarray, int or None (-> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_opts(flags=0, hub_threshold=0, lanes_per_row=0):
+    return gee_opts(flags, hub_threshold, lanes_per_row, 0)
+
+
+def _opts_ref(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, int):
+        opts = make_opts(opts)
+    return ctypes.byref(opts)
+
+
+# ---- one function per C entry point ----------------------------------------------------
+
+def gee_version() -> int:
+    return lib().gee_version()
+
+
+def gee_strerror(code: int) -> str:
+    return lib().gee_strerror(code).decode()
+
+
+def gee_workspace_size(E, N, K, weighted, opts=None) -> int:
+    return lib().gee_workspace_size(E, N, K, 1 if weighted else 0, _opts_ref(opts))
+
+
+def gee_host_workspace_size(E, N, K, weighted, opts=None) -> int:
+    return lib().gee_host_workspace_size(E, N, K, 1 if weighted else 0, _opts_ref(opts))
+
+
+def gee_embed(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_bytes, stream=None, d_status=None) -> int:
+    return lib().gee_embed(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
+                           ptr(workspace), workspace_bytes, stream_handle(stream), ptr(d_status))
+
+
+def gee_embed_timed(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_bytes, stream=None,
+                    d_status=None, phase_ms=None) -> int:
+    return lib().gee_embed_timed(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
+                                 ptr(workspace), workspace_bytes, stream_handle(stream), ptr(d_status),
+                                 ptr(phase_ms))
+
+
+def gee_build_csr(src, dst, w, E, N, labels, K, opts, rowptr, col, val, nk, deg, workspace, workspace_bytes,
+                  stream=None, d_status=None) -> int:
+    return lib().gee_build_csr(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(rowptr),
+                               ptr(col), ptr(val), ptr(nk), ptr(deg), ptr(workspace), workspace_bytes,
+                               stream_handle(stream), ptr(d_status))
+
+
+def gee_class_counts(rowptr, col, N, labels, K, C, stream=None) -> int:
+    return lib().gee_class_counts(ptr(rowptr), ptr(col), N, ptr(labels), K, ptr(C), stream_handle(stream))
+
+
+def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_bytes, stream=None,
+                   status=None) -> int:
+    return lib().gee_embed_host(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
+                                ptr(workspace), workspace_bytes, stream_handle(stream), ptr(status))

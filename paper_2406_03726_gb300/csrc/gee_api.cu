@@ -1,0 +1,540 @@
+// Host runtime and C ABI of libgee (see include/gee.h).
+//
+// A call is planned on the host (digit widths, split threshold, lanes per row, the
+// workspace layout) and then enqueued on the caller's stream as: one memset of the
+// zero-initialised part of the workspace, then k_prep, k_sort (1 or 2 passes),
+// k_rowscan, k_hubprep, k_wdeg (weighted Laplacian only) and k_spmm.  Nothing is
+// allocated and nothing synchronises, so the sequence can be captured in a CUDA graph.
+#include "gee_internal.cuh"
+#include "../../include/gee.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+namespace gee {
+
+cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st);
+cudaError_t launch_sort(const Ctx &c, int blocks, bool final_pass, cudaStream_t st);
+cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st);
+cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st);
+cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st);
+cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
+cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32_t N, const int32_t *y, int32_t K,
+                                int32_t *C, int blocks, cudaStream_t st);
+cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st);
+cudaError_t configure_kernels();
+int occupancy_spmm(bool smem_acc);
+int occupancy_wdeg();
+int occupancy_sort();
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct DeviceInfo {
+    bool ready = false;
+    int sms = 0;
+    int occ_spmm[2] = {1, 1};
+    int occ_wdeg = 1;
+    int occ_sort = 1;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+
+int device_info(DeviceInfo &out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GEE_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo &d = g_dev[dev];
+    if (!d.ready) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEE_ERR_CUDA;
+        if (configure_kernels() != cudaSuccess) return GEE_ERR_CUDA;
+        d.occ_spmm[0] = occupancy_spmm(false);
+        d.occ_spmm[1] = occupancy_spmm(true);
+        d.occ_wdeg = occupancy_wdeg();
+        d.occ_sort = occupancy_sort();
+        d.ready = true;
+    }
+    out = d;
+    return GEE_OK;
+}
+
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + kAlign - 1) & ~(kAlign - 1);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+int bitlen(uint32_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+int ilog2_pow2(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
+struct Shape {
+    int64_t E;
+    int32_t N, K;
+    bool weighted;
+};
+
+// Plan parameters that depend only on the graph and the options (never on the batch
+// it is part of, so a graph gives the same bits alone and in a batch).
+void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d) {
+    d.E = s.E;
+    d.N = s.N;
+    d.K = s.K;
+    d.flags = o.flags & GEE_ALL_OPTIONS;
+    d.nbits = std::max(1, bitlen(s.N > 0 ? (uint32_t)(s.N - 1) : 0u));
+    if (d.nbits <= kMaxDigitBits) {
+        d.npass = 1;
+        d.lbits = 0;
+        d.fbits = d.nbits;
+    } else {
+        d.npass = 2;
+        d.lbits = (d.nbits + 1) / 2;
+        d.fbits = d.nbits - d.lbits;
+    }
+    const double mean = s.N > 0 ? (double)s.E / (double)s.N : 0.0;
+    int lpr = o.lanes_per_row;
+    if (lpr <= 0) {
+        lpr = 1;
+        while (lpr < 32 && lpr * 8 < mean) lpr <<= 1;
+    }
+    lpr = std::min(32, std::max(1, lpr));
+    d.lpr_log2 = ilog2_pow2(lpr);
+    d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : 4096;
+    d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
+    d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
+    d.rows_per_item = kWarps * (32 >> d.lpr_log2);
+    d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
+}
+
+uint32_t hub_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / ((int64_t)d.hub_C + 1)); }
+uint32_t chunk_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / d.hub_C) + hub_cap_of(d) + 1; }
+
+// zero-initialised arrays of one graph
+void layout_zero(Bump &b, GraphDesc &d) {
+    d.status = b.take<uint32_t>(1);
+    d.rowcnt = b.take<int32_t>((size_t)d.N);
+    d.nk = b.take<int32_t>((size_t)d.K);
+    d.hist_lo = b.take<uint32_t>(d.npass == 2 ? (size_t)1 << d.lbits : 0);
+    d.hist_f = b.take<uint32_t>((size_t)1 << d.fbits);
+    d.lb_a = b.take<uint32_t>(d.npass == 2 ? ((size_t)d.tiles_e << d.lbits) : 0);
+    d.lb_f = b.take<uint32_t>((size_t)d.tiles_e << d.fbits);
+    d.lb_s = b.take<uint32_t>((size_t)d.tiles_n);
+}
+
+void layout_rest(Bump &b, GraphDesc &d, bool weighted) {
+    d.rowptr = b.take<int32_t>((size_t)d.N + 1);
+    d.col = b.take<int32_t>((size_t)d.E + 4);
+    d.val = weighted ? b.take<float>((size_t)d.E + 4) : nullptr;
+    d.tmpk = d.npass == 2 ? b.take<uint32_t>((size_t)d.E) : nullptr;
+    d.tmpw = (d.npass == 2 && weighted) ? b.take<float>((size_t)d.E) : nullptr;
+    d.deg = b.take<float>((size_t)d.N);
+    d.dinv = b.take<float>((size_t)d.N);
+    d.tab = b.take<int2>((size_t)d.N);
+}
+
+void layout_call_zero(Bump &b, CallBufs &cb) {
+    cb.cs = b.take<CallState>(1);
+    cb.arrive_deg = b.take<uint32_t>(cb.hub_cap);
+    cb.arrive_z = b.take<uint32_t>(cb.hub_cap);
+}
+
+void layout_call_rest(Bump &b, CallBufs &cb) {
+    cb.hubs = b.take<HubEntry>(cb.hub_cap);
+    cb.chunk_off = b.take<uint32_t>((size_t)cb.hub_cap + 1);
+    cb.part_deg = b.take<double>(cb.chunk_cap);
+    cb.part_z = b.take<float2>((size_t)cb.chunk_cap * (size_t)cb.kmax);
+}
+
+int check_shape(int64_t E, int32_t N, int32_t K) {
+    if (E < 0 || N < 0 || K < 1) return GEE_ERR_ARG;
+    if (N > GEE_MAX_N || E >= GEE_MAX_E || K > GEE_MAX_K) return GEE_ERR_TOO_LARGE;
+    return GEE_OK;
+}
+
+gee_opts opts_or_default(const gee_opts *o) {
+    gee_opts r;
+    std::memset(&r, 0, sizeof(r));
+    if (o) r = *o;
+    return r;
+}
+
+// Full single-graph plan over a workspace base (nullptr = sizing only).
+struct SinglePlan {
+    GraphDesc d;
+    CallBufs cb;
+    size_t zero_bytes = 0;
+    size_t total_bytes = 0;
+};
+
+void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p) {
+    std::memset(&p.d, 0, sizeof(p.d));
+    std::memset(&p.cb, 0, sizeof(p.cb));
+    plan_params(s, o, want_deg, p.d);
+    p.cb.hub_cap = hub_cap_of(p.d);
+    p.cb.chunk_cap = chunk_cap_of(p.d);
+    p.cb.kmax = s.K;
+    Bump b{base};
+    layout_call_zero(b, p.cb);
+    layout_zero(b, p.d);
+    p.zero_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+    layout_rest(b, p.d, s.weighted);
+    layout_call_rest(b, p.cb);
+    p.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+}
+
+int cuda_check(cudaError_t e) { return e == cudaSuccess ? GEE_OK : GEE_ERR_CUDA; }
+
+#define GEE_TRY(x)                 \
+    do {                           \
+        int _rc = (x);             \
+        if (_rc != GEE_OK) return _rc; \
+    } while (0)
+
+// Phases of one call, in launch order (GEE_PHASE_* in gee.h).
+enum Phase { kPhMemset = 0, kPhPrep, kPhSortA, kPhSortF, kPhRowscan, kPhHubprep, kPhWdeg, kPhSpmm, kNumPhases };
+
+// Optional per-phase timing: events[i] is recorded before phase i, events[kNumPhases]
+// after the last one; ran[i] tells whether phase i launched anything.
+struct PhaseEvents {
+    cudaEvent_t ev[kNumPhases + 1];
+    bool ran[kNumPhases];
+};
+
+inline int mark(PhaseEvents *pe, int ph, cudaStream_t st) {
+    if (!pe) return GEE_OK;
+    return cuda_check(cudaEventRecord(pe->ev[ph], st));
+}
+
+// Enqueue the whole path for one planned graph.
+int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe = nullptr) {
+    const GraphDesc &d = p.d;
+    Ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.g0 = d;
+    c.G = 1;
+    c.cb = p.cb;
+    if (pe) std::memset(pe->ran, 0, sizeof(pe->ran));
+    GEE_TRY(mark(pe, kPhMemset, st));
+    GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st)));
+    const int prep_items = (int)((d.E + kPrepTile - 1) / kPrepTile + ((int64_t)d.N + kPrepTile - 1) / kPrepTile);
+    c.items = prep_items;
+    GEE_TRY(mark(pe, kPhPrep, st));
+    GEE_TRY(cuda_check(launch_prep(c, prep_items, st)));
+    if (pe) pe->ran[kPhMemset] = true, pe->ran[kPhPrep] = prep_items > 0;
+    GEE_TRY(mark(pe, kPhSortA, st));
+    const int sort_grid = (int)std::min<int64_t>(d.tiles_e, (int64_t)dev.sms * dev.occ_sort);
+    if (d.tiles_e > 0 && d.npass == 2) {
+        c.items = d.tiles_e;
+        GEE_TRY(cuda_check(launch_sort(c, sort_grid, false, st)));
+        if (pe) pe->ran[kPhSortA] = true;
+    }
+    GEE_TRY(mark(pe, kPhSortF, st));
+    if (d.tiles_e > 0) {
+        c.items = d.tiles_e;
+        GEE_TRY(cuda_check(launch_sort(c, sort_grid, true, st)));
+        if (pe) pe->ran[kPhSortF] = true;
+    }
+    c.items = d.tiles_n;
+    GEE_TRY(mark(pe, kPhRowscan, st));
+    GEE_TRY(cuda_check(launch_rowscan(c, d.tiles_n, st)));
+    if (pe) pe->ran[kPhRowscan] = d.tiles_n > 0;
+    GEE_TRY(mark(pe, kPhHubprep, st));
+    if (p.cb.hub_cap > 0) {
+        GEE_TRY(cuda_check(launch_hubprep(p.cb, st)));
+        if (pe) pe->ran[kPhHubprep] = true;
+    }
+    const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
+    c.items = row_items;
+    const int64_t max_items = (int64_t)row_items + (p.cb.hub_cap > 0 ? p.cb.chunk_cap : 0);
+    GEE_TRY(mark(pe, kPhWdeg, st));
+    if (d.wdeg) {
+        const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
+        GEE_TRY(cuda_check(launch_wdeg(c, grid, st)));
+        if (pe) pe->ran[kPhWdeg] = grid > 0;
+    }
+    const bool smem = d.K > kRegK;
+    const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_spmm[smem ? 1 : 0]);
+    GEE_TRY(mark(pe, kPhSpmm, st));
+    GEE_TRY(cuda_check(launch_spmm(c, grid, smem, st)));
+    if (pe) pe->ran[kPhSpmm] = grid > 0;
+    GEE_TRY(mark(pe, kNumPhases, st));
+    return GEE_OK;
+}
+
+int check_ws(void *ws, size_t bytes, size_t need) {
+    if (need == 0) return GEE_OK;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) || bytes < need) return GEE_ERR_WORKSPACE;
+    return GEE_OK;
+}
+
+int check_inputs(const int32_t *src, const int32_t *dst, int64_t E, int32_t N, const int32_t *labels) {
+    if (E > 0 && (!src || !dst)) return GEE_ERR_ARG;
+    if (N > 0 && !labels) return GEE_ERR_ARG;
+    return GEE_OK;
+}
+
+}  // namespace
+}  // namespace gee
+
+using namespace gee;
+
+extern "C" {
+
+int gee_version(void) { return 100; }
+
+const char *gee_strerror(int code) {
+    switch (code) {
+        case GEE_OK: return "success";
+        case GEE_ERR_ARG: return "invalid argument";
+        case GEE_ERR_TOO_LARGE: return "size beyond the supported limits (N <= 2^21, E < 2^30, K <= 64)";
+        case GEE_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+        case GEE_ERR_CUDA: return "CUDA runtime error";
+        case GEE_ERR_DATA: return "the device reported invalid input data (see status bits)";
+        default: return "unknown error";
+    }
+}
+
+size_t gee_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts) {
+    if (check_shape(E, N, K) != GEE_OK) return 0;
+    SinglePlan p;
+    plan_single(Shape{E, N, K, weighted != 0}, opts_or_default(opts), false, nullptr, p);
+    return p.total_bytes;
+}
+
+}  // extern "C"
+
+namespace gee {
+namespace {
+int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+               const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
+               size_t workspace_bytes, void *stream, uint32_t *d_status, PhaseEvents *pe) {
+    GEE_TRY(check_shape(E, N, K));
+    GEE_TRY(check_inputs(d_src, d_dst, E, N, d_labels));
+    if (N > 0 && !d_Z) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    if (o.reserved != 0 || o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
+        (o.lanes_per_row & (o.lanes_per_row - 1)))
+        return GEE_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        if (pe) {
+            std::memset(pe->ran, 0, sizeof(pe->ran));
+            for (int i = 0; i <= kNumPhases; ++i) GEE_TRY(cuda_check(cudaEventRecord(pe->ev[i], st)));
+        }
+        if (d_status) return cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    SinglePlan p;
+    const Shape s{E, N, K, d_w != nullptr};
+    plan_single(s, o, false, nullptr, p);
+    GEE_TRY(check_ws(d_workspace, workspace_bytes, p.total_bytes));
+    plan_single(s, o, false, static_cast<char *>(d_workspace), p);
+    p.d.src = d_src;
+    p.d.dst = d_dst;
+    p.d.w = d_w;
+    p.d.y = d_labels;
+    p.d.Z = d_Z;
+    GEE_TRY(run_single(p, dev, st, pe));
+    if (d_status)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+}  // namespace
+}  // namespace gee
+
+extern "C" {
+
+int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+              const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
+              size_t workspace_bytes, void *stream, uint32_t *d_status) {
+    return embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes, stream,
+                      d_status, nullptr);
+}
+
+int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                    const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
+                    size_t workspace_bytes, void *stream, uint32_t *d_status, float *phase_ms) {
+    if (!phase_ms) return GEE_ERR_ARG;
+    PhaseEvents pe;
+    for (int i = 0; i <= kNumPhases; ++i)
+        if (cudaEventCreate(&pe.ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(pe.ev[j]);
+            return GEE_ERR_CUDA;
+        }
+    int rc = embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes, stream,
+                        d_status, &pe);
+    if (rc == GEE_OK && cudaEventSynchronize(pe.ev[kNumPhases]) != cudaSuccess) rc = GEE_ERR_CUDA;
+    for (int i = 0; i < kNumPhases; ++i) {
+        float ms = -1.0f;
+        if (rc == GEE_OK && pe.ran[i]) {
+            if (cudaEventElapsedTime(&ms, pe.ev[i], pe.ev[i + 1]) != cudaSuccess) ms = -1.0f;
+        }
+        phase_ms[i] = ms;
+    }
+    for (int i = 0; i <= kNumPhases; ++i) cudaEventDestroy(pe.ev[i]);
+    return rc;
+}
+
+int gee_build_csr(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                  const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_rowptr, int32_t *d_col,
+                  float *d_val, int32_t *d_nk, float *d_deg, void *d_workspace, size_t workspace_bytes, void *stream,
+                  uint32_t *d_status) {
+    GEE_TRY(check_shape(E, N, K));
+    GEE_TRY(check_inputs(d_src, d_dst, E, N, d_labels));
+    if (!d_rowptr || (E > 0 && !d_col)) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        GEE_TRY(cuda_check(cudaMemsetAsync(d_rowptr, 0, sizeof(int32_t), st)));
+        if (d_nk) GEE_TRY(cuda_check(cudaMemsetAsync(d_nk, 0, sizeof(int32_t) * K, st)));
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    SinglePlan p;
+    const Shape s{E, N, K, d_w != nullptr};
+    plan_single(s, o, true, nullptr, p);
+    GEE_TRY(check_ws(d_workspace, workspace_bytes, p.total_bytes));
+    plan_single(s, o, true, static_cast<char *>(d_workspace), p);
+    p.d.src = d_src;
+    p.d.dst = d_dst;
+    p.d.w = d_w;
+    p.d.y = d_labels;
+    p.d.Z = nullptr;
+    const GraphDesc &d = p.d;
+    Ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.g0 = d;
+    c.G = 1;
+    c.cb = p.cb;
+    GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st)));
+    const int prep_items = (int)((d.E + kPrepTile - 1) / kPrepTile + ((int64_t)d.N + kPrepTile - 1) / kPrepTile);
+    c.items = prep_items;
+    GEE_TRY(cuda_check(launch_prep(c, prep_items, st)));
+    if (d.tiles_e > 0) {
+        c.items = d.tiles_e;
+        const int sort_grid = (int)std::min<int64_t>(d.tiles_e, (int64_t)dev.sms * dev.occ_sort);
+        if (d.npass == 2) GEE_TRY(cuda_check(launch_sort(c, sort_grid, false, st)));
+        GEE_TRY(cuda_check(launch_sort(c, sort_grid, true, st)));
+    }
+    c.items = d.tiles_n;
+    GEE_TRY(cuda_check(launch_rowscan(c, d.tiles_n, st)));
+    if (d.wdeg) {
+        if (p.cb.hub_cap > 0) GEE_TRY(cuda_check(launch_hubprep(p.cb, st)));
+        const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
+        c.items = row_items;
+        const int64_t max_items = (int64_t)row_items + (p.cb.hub_cap > 0 ? p.cb.chunk_cap : 0);
+        const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
+        GEE_TRY(cuda_check(launch_wdeg(c, grid, st)));
+    }
+    GEE_TRY(cuda_check(cudaMemcpyAsync(d_rowptr, d.rowptr, sizeof(int32_t) * ((size_t)N + 1),
+                                       cudaMemcpyDeviceToDevice, st)));
+    if (E > 0) {
+        GEE_TRY(cuda_check(
+            cudaMemcpyAsync(d_col, d.col, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToDevice, st)));
+        if (d_val) {
+            if (d.val)
+                GEE_TRY(cuda_check(
+                    cudaMemcpyAsync(d_val, d.val, sizeof(float) * (size_t)E, cudaMemcpyDeviceToDevice, st)));
+            else
+                GEE_TRY(cuda_check(launch_fill(d_val, E, 1.0f, st)));
+        }
+    }
+    if (d_nk)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_nk, d.nk, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToDevice, st)));
+    if (d_deg)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_deg, d.deg, sizeof(float) * (size_t)N, cudaMemcpyDeviceToDevice, st)));
+    if (d_status)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+
+int gee_class_counts(const int32_t *d_rowptr, const int32_t *d_col, int32_t N, const int32_t *d_labels, int32_t K,
+                     int32_t *d_C, void *stream) {
+    if (N < 0 || K < 1) return GEE_ERR_ARG;
+    if (K > GEE_MAX_K || N > GEE_MAX_N) return GEE_ERR_TOO_LARGE;
+    if (N == 0) return GEE_OK;
+    if (!d_rowptr || !d_col || !d_labels || !d_C) return GEE_ERR_ARG;
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    const int blocks = (int)std::min<int64_t>(((int64_t)N + 3) / 4, (int64_t)dev.sms * 8);
+    return cuda_check(launch_class_counts(d_rowptr, d_col, N, d_labels, K, d_C, blocks,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t gee_host_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts) {
+    if (check_shape(E, N, K) != GEE_OK) return 0;
+    Bump b{nullptr};
+    b.take<int32_t>((size_t)E);
+    b.take<int32_t>((size_t)E);
+    if (weighted) b.take<float>((size_t)E);
+    b.take<int32_t>((size_t)N);
+    b.take<float>((size_t)N * (size_t)K);
+    b.take<uint32_t>(1);
+    const size_t head = (b.off + kAlign - 1) & ~(kAlign - 1);
+    return head + gee_workspace_size(E, N, K, weighted, opts);
+}
+
+int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
+                   const int32_t *labels, int32_t K, const gee_opts *opts, float *Z, void *d_workspace,
+                   size_t workspace_bytes, void *stream, uint32_t *status) {
+    GEE_TRY(check_shape(E, N, K));
+    GEE_TRY(check_inputs(src, dst, E, N, labels));
+    if (N > 0 && !Z) return GEE_ERR_ARG;
+    const size_t need = gee_host_workspace_size(E, N, K, w != nullptr, opts);
+    GEE_TRY(check_ws(d_workspace, workspace_bytes, need));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Bump b{static_cast<char *>(d_workspace)};
+    int32_t *d_src = b.take<int32_t>((size_t)E);
+    int32_t *d_dst = b.take<int32_t>((size_t)E);
+    float *d_w = w ? b.take<float>((size_t)E) : nullptr;
+    int32_t *d_y = b.take<int32_t>((size_t)N);
+    float *d_Z = b.take<float>((size_t)N * (size_t)K);
+    uint32_t *d_st = b.take<uint32_t>(1);
+    const size_t head = (b.off + kAlign - 1) & ~(kAlign - 1);
+    if (E > 0) {
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_src, src, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, st)));
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_dst, dst, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, st)));
+        if (w) GEE_TRY(cuda_check(cudaMemcpyAsync(d_w, w, sizeof(float) * (size_t)E, cudaMemcpyHostToDevice, st)));
+    }
+    if (N > 0)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_y, labels, sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, st)));
+    GEE_TRY(gee_embed(E > 0 ? d_src : nullptr, E > 0 ? d_dst : nullptr, d_w, E, N, d_y, K, opts, d_Z,
+                      static_cast<char *>(d_workspace) + head, workspace_bytes - head, stream, d_st));
+    uint32_t h_status = 0;
+    if (N > 0)
+        GEE_TRY(cuda_check(
+            cudaMemcpyAsync(Z, d_Z, sizeof(float) * (size_t)N * (size_t)K, cudaMemcpyDeviceToHost, st)));
+    GEE_TRY(cuda_check(cudaMemcpyAsync(&h_status, d_st, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)));
+    GEE_TRY(cuda_check(cudaStreamSynchronize(st)));
+    if (status) *status = h_status;
+    return h_status ? GEE_ERR_DATA : GEE_OK;
+}
+
+}  // extern "C"

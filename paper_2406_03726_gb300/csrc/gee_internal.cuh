@@ -1,0 +1,117 @@
+// Internal definitions shared by the GEE kernels and the host runtime.
+//
+// One "graph descriptor" (GraphDesc) carries a graph's inputs, its plan (digit widths,
+// split threshold, lanes per row) and the device pointers of its scratch arrays.  Every
+// kernel processes a flat list of work items that spans one or many graphs: item i
+// belongs to the graph g with prefix[g] <= i < prefix[g+1].  A single-graph call passes
+// its descriptor by value in the launch parameters, so it needs no host-to-device copy.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gee {
+
+// ---- tile geometry --------------------------------------------------------------------
+constexpr int kThreads = 256;                  // every kernel uses 256-thread CTAs
+constexpr int kWarps = kThreads / 32;
+constexpr int kSortItems = 16;                 // keys per thread in a sort pass
+constexpr int kSortTile = kThreads * kSortItems;   // 4096 edges per sort tile
+constexpr int kPrepTile = 8192;                // edges (or nodes) per histogram tile
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kThreads * kScanItems;   // 4096 nodes per scan tile
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxDigits = 1 << kMaxDigitBits;     // 2048 buckets per radix pass
+constexpr int kMaxK = 64;
+constexpr int kRegK = 8;                       // K <= 8: per-lane register accumulators
+
+// ---- look-back status words (one 32-bit word per tile x bucket) -------------------------
+// bits 31..30: 0 = nothing published, 1 = tile aggregate, 2 = inclusive prefix
+// bits 29..0 : the count (edge counts are < 2^30)
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr int kSpinLimit = 1 << 22;            // bounded waits: ~1 s, then GEE_STATUS_TIMEOUT
+
+// status bits (must equal GEE_STATUS_* in gee.h)
+constexpr uint32_t kStIndex = 1u, kStLabel = 2u, kStWeight = 4u, kStTimeout = 8u;
+constexpr uint32_t kOptAug = 1u, kOptLap = 2u, kOptCor = 4u;
+
+struct GraphDesc {
+    // inputs (device)
+    const int32_t *src, *dst;
+    const float *w;          // nullptr = unweighted
+    const int32_t *y;
+    float *Z;
+    int64_t E;
+    int32_t N, K;
+    uint32_t flags;
+    // plan
+    int32_t nbits;           // bits of a node id (>= 1)
+    int32_t npass;           // radix passes: 1 (nbits <= 11) or 2
+    int32_t lbits;           // digit bits of the first pass (2-pass graphs)
+    int32_t fbits;           // digit bits of the final pass
+    int32_t hub_C;           // rows longer than this are split into chunks of hub_C
+    int32_t lpr_log2;        // log2(lanes cooperating on one light row)
+    int32_t tiles_e;         // ceil(E / kSortTile)
+    int32_t tiles_n;         // ceil(N / kScanTile)
+    int32_t rows_per_item;   // light rows per SpMM work item
+    int32_t wdeg;            // 1: degrees and node table come from k_wdeg (weighted + Laplacian)
+    // scratch (device)
+    int32_t *rowptr;         // [N+1]
+    int32_t *rowcnt;         // [N]           zeroed
+    int32_t *col;            // [E + 4]
+    float *val;              // [E + 4]       weighted only
+    uint32_t *tmpk;          // [E]           2-pass: (src >> lbits) << nbits | dst
+    float *tmpw;             // [E]           2-pass weighted
+    uint32_t *hist_lo;       // [2^lbits]     zeroed
+    uint32_t *hist_f;        // [2^fbits]     zeroed
+    uint32_t *lb_a;          // [tiles_e << lbits] zeroed
+    uint32_t *lb_f;          // [tiles_e << fbits] zeroed
+    uint32_t *lb_s;          // [tiles_n]     zeroed
+    int32_t *nk;             // [K]           zeroed
+    float *deg;              // [N]  D_ii
+    float *dinv;             // [N]  D_ii^-1/2 (1 without the Laplacian)
+    int2 *tab;               // [N]  {class or 0, s_j as float bits (0 if unlabelled)}
+    uint32_t *status;        // [1]           zeroed
+};
+
+// Per-call state shared by all graphs of a launch sequence (zeroed at the start).
+struct CallState {
+    uint32_t ctr[8];         // work-stealing / tile-id counters, one per kernel
+    uint32_t hub_count;      // rows longer than their graph's hub_C
+    uint32_t hub_chunks;     // total chunks over those rows
+    uint32_t pad[6];
+};
+
+struct HubEntry {
+    int32_t g, row, len, nch;
+};
+
+struct CallBufs {
+    CallState *cs;           // zeroed
+    HubEntry *hubs;          // [hub_cap]
+    uint32_t *chunk_off;     // [hub_cap + 1]
+    uint32_t *arrive_deg;    // [hub_cap] zeroed
+    uint32_t *arrive_z;      // [hub_cap] zeroed
+    double *part_deg;        // [chunk_cap]
+    float2 *part_z;          // [chunk_cap * kmax]
+    uint32_t hub_cap, chunk_cap;
+    int32_t kmax;            // largest K in the call
+    int32_t pad;
+};
+
+// Launch context: which graphs, and how this kernel's items map onto them.
+struct Ctx {
+    GraphDesc g0;            // the graph when G == 1
+    const GraphDesc *graphs; // device array [G] when G > 1
+    const int32_t *prefix;   // device [G+1] item prefix for this kernel (G > 1)
+    int32_t G;
+    int32_t items;           // total items of this kernel (host-known part)
+    CallBufs cb;
+};
+
+// item prefixes stored per kernel for batched calls
+enum PrefixKind { kPfxPrep = 0, kPfxSortA = 1, kPfxSortF = 2, kPfxScan = 3, kPfxRows = 4, kPfxWRows = 5, kNumPfx = 6 };
+
+}  // namespace gee

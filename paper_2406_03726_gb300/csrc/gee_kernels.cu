@@ -1,0 +1,1459 @@
+// Device kernels of the sparse GEE path (Qin & Shen, Section 2 Eq. 1, Table 1, Section 3).
+//
+//   k_prep     label counts n_k (definition of W), input checks, radix-digit histograms of
+//              the source ids
+//   k_sort     one stable LSD radix pass over the edges, keyed by source id, tile by tile
+//              with decoupled look-back; the final pass writes the CSR (col_indices, data)
+//              and the row lengths
+//   k_rowscan  index_pointers by a look-back scan of the row lengths; unweighted degrees
+//              D_ii and the node table s_j = D_jj^-1/2 / n_{y_j}; hub-row list
+//   k_hubprep  chunk offsets of the split (hub) rows
+//   k_wdeg     weighted degrees: FP32 compensated sums on light rows, FP64 chunk
+//              partials merged in FP64 on hub rows; then D^-1/2 and the node table
+//   k_spmm     Z = D^-1/2 (A + I) D^-1/2 W as a label-gather over the CSR rows, with the
+//              augmentation term, the D_ii^-1/2 scaling and the row 2-norm (correlation)
+//              fused into the epilogue; hub rows are split across CTAs and merged with
+//              two-sum compensation by the last CTA to finish
+//
+// Every inter-CTA wait is bounded (kSpinLimit) and records kStTimeout instead of hanging;
+// every global index derived from data is range-checked, so bad input cannot make a
+// kernel touch memory outside its buffers.
+#include "gee_internal.cuh"
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace gee {
+
+// ------------------------------------------------------------------------------------
+// small device helpers
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// streaming loads of data read exactly once (no L1 allocation)
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int4 ld_stream4(const int32_t *p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream4(const float *p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int find_graph(const int32_t *prefix, int G, int item) {
+    int lo = 0, hi = G;  // largest g with prefix[g] <= item
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Copy graph g's descriptor to shared memory (thread 0 resolves the item) and return the
+// item's index local to that graph.  Contains __syncthreads.
+__device__ __forceinline__ int load_desc(const Ctx &c, int item, GraphDesc *sg, int *sl,
+                                         const int32_t *prefix) {
+    if (threadIdx.x == 0) {
+        int g = 0, base = 0;
+        if (c.G > 1) {
+            g = find_graph(prefix, c.G, item);
+            base = __ldg(prefix + g);
+            *sg = c.graphs[g];
+        } else {
+            *sg = c.g0;
+        }
+        sl[0] = item - base;
+        sl[1] = g;
+    }
+    __syncthreads();
+    return sl[0];
+}
+
+__device__ __forceinline__ void load_desc_idx(const Ctx &c, int g, GraphDesc *sg) {
+    if (threadIdx.x == 0) *sg = (c.G > 1) ? c.graphs[g] : c.g0;
+    __syncthreads();
+}
+
+// Exclusive scan over the 256 threads of a CTA; returns the thread's prefix and the total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) {
+        uint32_t s = s_warp[i];
+        before += (i < w) ? s : 0u;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return before + x - v;
+}
+
+// Decoupled look-back over the tiles before `t` for one bucket: the sum of their counts.
+__device__ __forceinline__ uint32_t look_back(const uint32_t *lb, int width, int t, int d, uint32_t &err) {
+    uint32_t excl = 0;
+    int j = t - 1, spins = 0;
+    while (j >= 0) {
+        uint32_t s = ld_relaxed(lb + (size_t)j * width + d);
+        uint32_t f = s & ~kValMask;
+        if (f == 0u) {
+            if (++spins > kSpinLimit) {
+                err |= kStTimeout;
+                break;
+            }
+            if (spins > 64) __nanosleep(128);
+            continue;
+        }
+        excl += s & kValMask;
+        if (f == kFlagPre) break;
+        --j;
+    }
+    return excl;
+}
+
+// Error-free transformation: s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    float s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+__device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
+
+// ------------------------------------------------------------------------------------
+// k_prep: histograms of source-id digits (edge tiles), class sizes n_k (node tiles)
+
+constexpr int kPrivDigits = 512;  // digit counts up to this get one private histogram per warp
+
+__global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ uint32_t h_lo[kWarps * kPrivDigits];
+    __shared__ uint32_t h_f[kWarps * kPrivDigits];
+    __shared__ uint32_t s_err;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    if (tid == 0) s_err = 0;
+    uint32_t err = 0;
+    const int64_t tiles_p = (sg.E + kPrepTile - 1) / kPrepTile;
+    if (t < tiles_p) {
+        const bool two = sg.npass == 2;
+        const int Dl = two ? (1 << sg.lbits) : 0, Df = 1 << sg.fbits;
+        // private per-warp histograms when they fit, one shared histogram otherwise
+        const int strl = (Dl <= kPrivDigits) ? Dl : 0, strf = (Df <= kPrivDigits) ? Df : 0;
+        const int nl = strl ? kWarps * Dl : Dl, nf = strf ? kWarps * Df : Df;
+        for (int i = tid; i < nf; i += kThreads) h_f[i] = 0;
+        for (int i = tid; i < nl; i += kThreads) h_lo[i] = 0;
+        __syncthreads();
+        uint32_t *hl = h_lo + warp * strl, *hf = h_f + warp * strf;
+        const int64_t e0 = (int64_t)t * kPrepTile;
+        const int n = (int)min64(kPrepTile, sg.E - e0);
+        const int32_t *s = sg.src + e0;
+        const uint32_t N = (uint32_t)sg.N;
+        const int lb = sg.lbits;
+        const uint32_t lm = (1u << lb) - 1u;
+        auto add = [&](int v) {
+            if ((uint32_t)v >= N) {
+                err |= kStIndex;
+                v = 0;
+            }
+            if (two) {
+                atomicAdd(&hl[(uint32_t)v & lm], 1u);
+                atomicAdd(&hf[(uint32_t)v >> lb], 1u);
+            } else {
+                atomicAdd(&hf[v], 1u);
+            }
+        };
+        if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0) {
+            constexpr int kV = kPrepTile / (4 * kThreads);  // 8 vectors of 4 ids per thread
+            const int nv = n >> 2;
+            int4 v[kV];
+#pragma unroll
+            for (int k = 0; k < kV; ++k) {
+                const int vi = tid + k * kThreads;
+                v[k] = vi < nv ? ld_stream4(s + 4 * vi) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kV; ++k) {
+                if (tid + k * kThreads < nv) {
+                    add(v[k].x);
+                    add(v[k].y);
+                    add(v[k].z);
+                    add(v[k].w);
+                }
+            }
+            if (tid < n - 4 * nv) add(ld_stream(s + 4 * nv + tid));
+        } else {
+            for (int i = tid; i < n; i += kThreads) add(ld_stream(s + i));
+        }
+        __syncthreads();
+        for (int d = tid; d < Df; d += kThreads) {
+            uint32_t v = 0;
+            if (strf)
+                for (int w = 0; w < kWarps; ++w) v += h_f[w * Df + d];
+            else
+                v = h_f[d];
+            if (v) atomicAdd(&sg.hist_f[d], v);
+        }
+        for (int d = tid; d < Dl; d += kThreads) {
+            uint32_t v = 0;
+            if (strl)
+                for (int w = 0; w < kWarps; ++w) v += h_lo[w * Dl + d];
+            else
+                v = h_lo[d];
+            if (v) atomicAdd(&sg.hist_lo[d], v);
+        }
+    } else {
+        const int64_t n0 = (int64_t)(t - tiles_p) * kPrepTile;
+        const int n = (int)min64(kPrepTile, (int64_t)sg.N - n0);
+        const int K = sg.K;
+        for (int i = tid; i < K; i += kThreads) h_f[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += kThreads) {
+            int yv = __ldg(sg.y + n0 + i);
+            if (yv < -1 || yv >= K) err |= kStLabel;
+            else if (yv >= 0) atomicAdd(&h_f[yv], 1u);
+        }
+        __syncthreads();
+        for (int i = tid; i < K; i += kThreads)
+            if (h_f[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h_f[i]);
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
+}
+
+// ------------------------------------------------------------------------------------
+// TMA bulk copies (global -> shared memory, completion counted on an mbarrier)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase `parity` of an mbarrier; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 16) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Windowed decoupled look-back: the predecessors' statuses are read 8 at a time, so a
+// chain of aggregates costs one round trip per 8 tiles.
+__device__ __forceinline__ uint32_t look_back8(const uint32_t *lb, int width, int t, int d, uint32_t &err) {
+    uint32_t excl = 0;
+    int j = t - 1, spins = 0;
+    while (j >= 0) {
+        uint32_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (j - q >= 0) ? ld_relaxed(lb + (size_t)(j - q) * width + d) : kFlagPre;
+        int q = 0;
+        bool done = false;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (done || q != r) continue;
+            const uint32_t f = v[r] & ~kValMask;
+            if (f == 0u) continue;  // not published yet: stop here, q stays r
+            excl += v[r] & kValMask;
+            if (f == kFlagPre) done = true;
+            q = r + 1;
+        }
+        if (done) break;
+        j -= q;
+        if (q == 0) {
+            if (++spins > kSpinLimit) {
+                err |= kStTimeout;
+                break;
+            }
+            if (spins > 16) __nanosleep(64);
+        }
+    }
+    return excl;
+}
+
+// ------------------------------------------------------------------------------------
+// k_sort: one stable radix pass over the edges of one or many graphs.
+//
+//   FINAL = false  first of two passes (graphs with more than 2^11 nodes): digit = low
+//                  lbits of the source id; edge list -> packed ((src >> lbits) << nbits |
+//                  dst) + weight, in digit order.
+//   FINAL = true   last pass: 1-pass graphs read the edge list (digit = source id), 2-pass
+//                  graphs read the packed array (digit = high bits); writes col/val at their
+//                  CSR positions and adds each tile's row-run lengths to rowcnt.
+//
+// Persistent CTAs claim 4096-edge tiles in order.  While a tile is ranked and scattered,
+// the next claimed tile streams into shared memory by TMA bulk copies.  Warp w ranks tile
+// elements [512 w, 512 w + 512), item i of lane l being element 512 w + 32 i + l, with
+// match.any in input order, so ranks are stable.  Bucket offsets across tiles come from a
+// decoupled look-back on per-(tile, digit) status words.
+
+constexpr int kStreamWords = kSortTile;                         // one stream = 4096 words
+constexpr size_t kStageBytes = (size_t)3 * kStreamWords * 4;     // src|tmpk, dst, w|tmpw
+constexpr size_t kWorkBytes = (size_t)3 * kSortTile * 4;         // union, see below
+constexpr size_t kSortSmem = kStageBytes + kWorkBytes + (size_t)2 * kMaxDigits * 4;
+
+struct SortTileInfo {
+    int t;         // tile index within its graph
+    int g;         // graph index
+    int n;         // edges in the tile
+    int staged;    // 1: the first (n & ~3) edges are in the stage buffers
+};
+
+template <bool FINAL>
+__device__ __forceinline__ void sort_issue_stage(const GraphDesc &g, int t, uint32_t *stage, uint64_t *bar,
+                                                 SortTileInfo &info) {
+    const bool coo = !FINAL || g.npass == 1;
+    const int64_t e0 = (int64_t)t * kSortTile;
+    const int n = (int)min64(kSortTile, g.E - e0);
+    const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
+    const void *p0 = coo ? (const void *)(g.src + e0) : (const void *)(g.tmpk + e0);
+    const void *p1 = coo ? (const void *)(g.dst + e0) : nullptr;
+    const void *p2 = g.w ? (coo ? (const void *)(g.w + e0) : (const void *)(g.tmpw + e0)) : nullptr;
+    const bool ok = bytes > 0 && aligned16(p0) && (!p1 || aligned16(p1)) && (!p2 || aligned16(p2));
+    info.t = t;
+    info.n = n;
+    info.staged = ok ? 1 : 0;
+    if (ok) {
+        fence_proxy_async();  // earlier generic reads of the stage precede these async writes
+        const uint32_t nstreams = 1u + (p1 ? 1u : 0u) + (p2 ? 1u : 0u);
+        mbar_expect_tx(bar, bytes * nstreams);
+        bulk_g2s(stage, p0, bytes, bar);
+        if (p1) bulk_g2s(stage + kStreamWords, p1, bytes, bar);
+        if (p2) bulk_g2s(stage + 2 * kStreamWords, p2, bytes, bar);
+    }
+}
+
+template <bool FINAL>
+__global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    unsigned char *work = smem + kStageBytes;
+    // union member 1 (ranking): per-warp digit counters, tile starts, first-pass bases
+    uint16_t *wcnt = reinterpret_cast<uint16_t *>(work);
+    uint32_t *tstart = reinterpret_cast<uint32_t *>(work + (size_t)kWarps * kMaxDigits * 2);
+    uint32_t *lobase = tstart + kMaxDigits;
+    // union member 2 (scatter): the tile sorted by digit
+    uint32_t *skey = reinterpret_cast<uint32_t *>(work);
+    uint32_t *spay = skey + kSortTile;
+    float *sw = reinterpret_cast<float *>(spay + kSortTile);
+    uint32_t *dglob = reinterpret_cast<uint32_t *>(work + kWorkBytes);
+    uint32_t *dbase = dglob + kMaxDigits;
+
+    __shared__ GraphDesc sgd[2];
+    __shared__ SortTileInfo sinfo[2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item;
+    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t s_err;
+    __shared__ uint32_t s_lo_first, s_lo_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ctr = FINAL ? 1 : 0;
+    uint32_t err = 0;
+    bool stage_timeout = false;
+
+    // resolve work item -> graph descriptor (tid 0 only)
+    auto resolve = [&](int item, int slot) {
+        int g = 0, base = 0;
+        if (c.G > 1) {
+            g = find_graph(c.prefix, c.G, item);
+            base = __ldg(c.prefix + g);
+            sgd[slot] = c.graphs[g];
+        } else {
+            sgd[slot] = c.g0;
+        }
+        sinfo[slot].g = g;
+        sort_issue_stage<FINAL>(sgd[slot], item - base, stage, &bar, sinfo[slot]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_err = 0;
+        s_item = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
+        if (s_item < c.items) resolve(s_item, 0);
+    }
+    __syncthreads();
+    if (s_item >= c.items) return;
+
+    int cur = 0;
+    int cached_g = -1;
+    uint32_t parity = 0;
+    for (;;) {
+        const GraphDesc &sg = sgd[cur];
+        const SortTileInfo info = sinfo[cur];
+        const int t = info.t, n = info.n;
+        const bool coo = !FINAL || sg.npass == 1;
+        const bool final2 = FINAL && sg.npass == 2;
+        const int bits = FINAL ? sg.fbits : sg.lbits;
+        const int D = 1 << bits;
+        const int nb = sg.nbits, lb = sg.lbits;
+        const uint32_t nmask = (1u << nb) - 1u;  // nb <= 21
+        const int64_t e0 = (int64_t)t * kSortTile;
+        const bool has_w = sg.w != nullptr;
+        const bool lap = (sg.flags & kOptLap) != 0;
+        const uint32_t N = (uint32_t)sg.N;
+        uint32_t *lb_st = FINAL ? sg.lb_f : sg.lb_a;
+        const int dpt = (D + kThreads - 1) / kThreads;
+        const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
+
+        // ---- per-graph bucket bases (exclusive scan of the pass histogram), cached
+        if (info.g != cached_g) {
+            const uint32_t *ghist = FINAL ? sg.hist_f : sg.hist_lo;
+            uint32_t loc = 0;
+            for (int d = dlo; d < dhi; ++d) loc += __ldcg(ghist + d);
+            uint32_t tot;
+            uint32_t run = block_excl_scan(loc, s_scan, tot);
+            for (int d = dlo; d < dhi; ++d) {
+                dbase[d] = run;
+                run += __ldcg(ghist + d);
+            }
+            cached_g = info.g;
+        }
+        // ---- zero the counters; bases of the first pass for 2-pass final tiles
+        for (int i = tid; i < kWarps * D; i += kThreads) wcnt[i] = 0;
+        if (final2) {
+            const int Dl = 1 << lb;
+            const int lpt = (Dl + kThreads - 1) / kThreads;
+            const int llo = min(Dl, tid * lpt), lhi = min(Dl, llo + lpt);
+            uint32_t loc = 0;
+            for (int d = llo; d < lhi; ++d) loc += __ldcg(sg.hist_lo + d);
+            uint32_t tot;
+            uint32_t run = block_excl_scan(loc, s_scan, tot);
+            for (int d = llo; d < lhi; ++d) {
+                lobase[d] = run;
+                run += __ldcg(sg.hist_lo + d);
+            }
+            __syncthreads();
+            if (tid < 2) {
+                const uint32_t p = (uint32_t)(e0 + (tid == 0 ? 0 : max(n - 1, 0)));
+                int a = 0, b = Dl;  // largest d with lobase[d] <= p
+                while (b - a > 1) {
+                    const int m = (a + b) >> 1;
+                    if (lobase[m] <= p) a = m;
+                    else b = m;
+                }
+                if (tid == 0) s_lo_first = a;
+                else s_lo_last = a;
+            }
+        }
+        // ---- wait for this tile's stage
+        if (info.staged) {
+            if (!mbar_wait(&bar, parity)) {
+                err |= kStTimeout;
+                stage_timeout = true;
+            }
+            parity ^= 1u;
+        }
+        __syncthreads();
+
+        // ---- load the 16 elements of this thread (stage, or global for the tail)
+        const int nst = info.staged ? (n & ~3) : 0;
+        uint32_t key[kSortItems], pay[kSortItems];
+        float wv[kSortItems];
+        const int wbase = warp * (32 * kSortItems);
+        if (coo) {
+            const uint32_t lm = (1u << lb) - 1u;
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const int idx = wbase + i * 32 + lane;
+                key[i] = 0xffffffffu;
+                pay[i] = 0;
+                wv[i] = 1.0f;
+                if (idx < n) {
+                    uint32_t s, d;
+                    float x = 1.0f;
+                    if (idx < nst) {
+                        s = stage[idx];
+                        d = stage[kStreamWords + idx];
+                        if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
+                    } else {
+                        s = (uint32_t)ld_stream(sg.src + e0 + idx);
+                        d = (uint32_t)ld_stream(sg.dst + e0 + idx);
+                        if (has_w) x = ld_stream(sg.w + e0 + idx);
+                    }
+                    if (s >= N) { err |= kStIndex; s = 0; }
+                    if (d >= N) { err |= kStIndex; d = 0; }
+                    if (has_w && (!finite_f(x) || (lap && x < 0.0f))) err |= kStWeight;
+                    if (FINAL) {
+                        key[i] = s;
+                        pay[i] = d;
+                    } else {
+                        key[i] = s & lm;
+                        pay[i] = ((s >> lb) << nb) | d;
+                    }
+                    wv[i] = x;
+                }
+            }
+        } else {
+            const uint32_t lof = s_lo_first, lol = s_lo_last;
+            const int Dl = 1 << lb;
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const int idx = wbase + i * 32 + lane;
+                key[i] = 0xffffffffu;
+                pay[i] = 0;
+                wv[i] = 1.0f;
+                if (idx < n) {
+                    uint32_t pk;
+                    float x = 1.0f;
+                    if (idx < nst) {
+                        pk = stage[idx];
+                        if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
+                    } else {
+                        pk = ld_stream(sg.tmpk + e0 + idx);
+                        if (has_w) x = ld_stream(sg.tmpw + e0 + idx);
+                    }
+                    uint32_t hi = pk >> nb;
+                    uint32_t d = pk & nmask;
+                    if (hi >= (uint32_t)D || d >= N) {  // only after an earlier failure
+                        err |= kStTimeout;
+                        hi &= (uint32_t)(D - 1);
+                        d = 0;
+                    }
+                    uint32_t lo = lof;
+                    if (lol != lof) {
+                        const uint32_t p = (uint32_t)(e0 + idx);
+                        int a = (int)lof, b = min((int)lol + 1, Dl);
+                        while (b - a > 1) {
+                            const int m = (a + b) >> 1;
+                            if (lobase[m] <= p) a = m;
+                            else b = m;
+                        }
+                        lo = (uint32_t)a;
+                    }
+                    pay[i] = d;
+                    key[i] = (hi << lb) | lo;
+                    wv[i] = x;
+                }
+            }
+        }
+        __syncthreads();  // stage consumed, counters zeroed
+
+        // ---- claim the next tile and start streaming it into the stage
+        if (tid == 0) {
+            s_item = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
+            if (s_item < c.items) resolve(s_item, cur ^ 1);
+        }
+
+        // ---- rank within the warp, in input order
+        uint32_t rank[kSortItems];
+        const unsigned lt = lanemask_lt();
+        uint16_t *mycnt = wcnt + warp * D;
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            const bool valid = key[i] != 0xffffffffu;
+            const uint32_t d = valid ? (final2 ? (key[i] >> lb) : key[i]) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = valid ? (uint32_t)mycnt[d] : 0u;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) mycnt[d] = (uint16_t)(before + __popc(peers));
+            __syncwarp();
+            rank[i] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+
+        // ---- per digit: warp offsets, tile counts, tile-local starts
+        uint32_t tcount[8];  // counts of the owned digits (dpt <= 8)
+        uint32_t loc = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int d = dlo + j;
+            uint32_t sum = 0;
+            if (d < dhi) {
+                for (int w = 0; w < kWarps; ++w) {
+                    const uint32_t cnt = wcnt[w * D + d];
+                    wcnt[w * D + d] = (uint16_t)sum;
+                    sum += cnt;
+                }
+            }
+            tcount[j] = sum;
+            loc += sum;
+        }
+        {
+            uint32_t tot;
+            uint32_t run = block_excl_scan(loc, s_scan, tot);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int d = dlo + j;
+                if (d < dhi) {
+                    tstart[d] = run;
+                    run += tcount[j];
+                }
+            }
+        }
+
+        // ---- decoupled look-back across tiles, per digit
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int d = dlo + j;
+            if (d < dhi) st_relaxed(lb_st + (size_t)t * D + d, (t == 0 ? kFlagPre : kFlagAgg) | tcount[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int d = dlo + j;
+            if (d < dhi) {
+                uint32_t ex = 0;
+                if (t > 0) {
+                    ex = look_back8(lb_st, D, t, d, err);
+                    st_relaxed(lb_st + (size_t)t * D + d, kFlagPre | ((ex + tcount[j]) & kValMask));
+                }
+                dglob[d] = dbase[d] + ex - tstart[d];
+            }
+        }
+        __syncthreads();
+
+        // ---- tile-local slot of each element (registers), then scatter into shared memory
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            if (key[i] != 0xffffffffu) {
+                const uint32_t d = final2 ? (key[i] >> lb) : key[i];
+                rank[i] += tstart[d] + wcnt[warp * D + d];
+            }
+        }
+        __syncthreads();  // counters dead: the sorted tile reuses their space
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            if (key[i] != 0xffffffffu) {
+                const uint32_t s = rank[i];
+                skey[s] = key[i];
+                spay[s] = pay[i];
+                sw[s] = wv[i];
+            }
+        }
+        __syncthreads();
+
+        // ---- write out: consecutive sorted slots of one digit go to consecutive addresses
+        const uint32_t E32 = (uint32_t)sg.E;
+        for (int s = tid; s < n; s += kThreads) {
+            const uint32_t k = skey[s];
+            const uint32_t d = final2 ? (k >> lb) : k;
+            const uint32_t pos = dglob[d] + (uint32_t)s;
+            if (pos >= E32) {
+                err |= kStTimeout;
+                continue;
+            }
+            if (FINAL) {
+                sg.col[pos] = (int32_t)spay[s];
+                if (has_w) sg.val[pos] = sw[s];
+            } else {
+                sg.tmpk[pos] = spay[s];
+                if (has_w) sg.tmpw[pos] = sw[s];
+            }
+        }
+
+        // ---- row lengths (final pass): runs of equal source id in the sorted tile
+        if (FINAL) {
+            if (!final2) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int d = dlo + j;
+                    if (d < dhi && tcount[j]) atomicAdd(sg.rowcnt + d, (int)tcount[j]);
+                }
+            } else {
+                for (int s = tid; s < n; s += kThreads) {
+                    const uint32_t k = skey[s];
+                    if (k >= N) continue;
+                    const bool st = (s == 0) || skey[s - 1] != k;
+                    const bool en = (s == n - 1) || skey[s + 1] != k;
+                    if (st && en) atomicAdd(sg.rowcnt + k, 1);
+                    else {
+                        if (st) atomicAdd(sg.rowcnt + k, -s);
+                        if (en) atomicAdd(sg.rowcnt + k, s + 1);
+                    }
+                }
+            }
+        }
+        if (err) {
+            atomicOr(&s_err, err);
+            err = 0;
+        }
+        __syncthreads();
+        if (tid == 0 && s_err) {
+            atomicOr(sg.status, s_err);
+            s_err = 0;
+        }
+        const bool more = s_item < c.items;
+        __syncthreads();
+        if (!more) break;
+        cur ^= 1;
+    }
+    (void)stage_timeout;
+}
+
+// ------------------------------------------------------------------------------------
+// node-table helpers
+
+// s_j = D_jj^-1/2 / n_{y_j} (Laplacian) or 1 / n_{y_j}; unlabelled nodes get {0, 0}
+__device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float deg, bool lap) {
+    const float dv = lap ? (deg > 0.0f ? 1.0f / sqrtf(deg) : 0.0f) : 1.0f;
+    int yv = __ldg(g.y + j);
+    int2 tv = make_int2(0, 0);
+    if (yv >= 0 && yv < g.K) {
+        const int cnt = __ldcg(g.nk + yv);
+        const float s = cnt > 0 ? dv / (float)cnt : 0.0f;
+        tv = make_int2(yv, __float_as_int(s));
+    }
+    g.deg[j] = deg;
+    g.dinv[j] = dv;
+    g.tab[j] = tv;
+}
+
+// ------------------------------------------------------------------------------------
+// k_rowscan: rowptr = exclusive scan of rowcnt (look-back across 4096-node tiles)
+
+__global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ int s_item;
+    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t s_excl;
+    __shared__ int32_t buf[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_err;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_item = (int)atomicAdd(&c.cb.cs->ctr[2], 1u);
+        s_err = 0;
+    }
+    __syncthreads();
+    const int t = load_desc(c, s_item, &sg, sl, c.prefix);
+    const int64_t n0 = (int64_t)t * kScanTile;
+    const int n = (int)min64(kScanTile, (int64_t)sg.N - n0);
+    auto pad = [](int i) { return i + (i >> 5); };
+    for (int i = tid; i < kScanTile; i += kThreads) buf[pad(i)] = (i < n) ? __ldcg(sg.rowcnt + n0 + i) : 0;
+    __syncthreads();
+    uint32_t loc = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) loc += (uint32_t)buf[pad(tid * kScanItems + j)];
+    uint32_t tot;
+    uint32_t run = block_excl_scan(loc, s_scan, tot);
+    uint32_t err = 0;
+    if (tid == 0) {
+        uint32_t ex = 0;
+        st_relaxed(sg.lb_s + t, (t == 0 ? kFlagPre : kFlagAgg) | tot);
+        if (t > 0) {
+            ex = look_back(sg.lb_s, 1, t, 0, err);
+            st_relaxed(sg.lb_s + t, kFlagPre | ((ex + tot) & kValMask));
+        }
+        s_excl = ex;
+    }
+    __syncthreads();
+    run += s_excl;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int i = pad(tid * kScanItems + j);
+        const uint32_t cnt = (uint32_t)buf[i];
+        buf[i] = (int32_t)run;
+        run += cnt;
+    }
+    __syncthreads();
+    const bool lap = (sg.flags & kOptLap) != 0;
+    const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
+    for (int i = tid; i < n; i += kThreads) {
+        const int64_t j = n0 + i;
+        const int32_t start = buf[pad(i)];
+        sg.rowptr[j] = start;
+        const int32_t cnt = __ldcg(sg.rowcnt + j);
+        if (i == n - 1 && n0 + n == sg.N) sg.rowptr[sg.N] = start + cnt;
+        if (cnt > sg.hub_C) {
+            const uint32_t h = atomicAdd(&c.cb.cs->hub_count, 1u);
+            if (h < c.cb.hub_cap) {
+                HubEntry he;
+                he.g = sl[1];
+                he.row = (int32_t)j;
+                he.len = cnt;
+                he.nch = (cnt + sg.hub_C - 1) / sg.hub_C;
+                c.cb.hubs[h] = he;
+            } else {
+                err |= kStTimeout;  // capacity is sized so this cannot happen
+            }
+        }
+        if (!sg.wdeg) write_node(sg, j, (float)cnt + aug, lap);
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
+}
+
+// ------------------------------------------------------------------------------------
+// k_hubprep: chunk offsets of the hub rows (one CTA)
+
+__global__ void __launch_bounds__(kThreads) k_hubprep(CallBufs cb) {
+    __shared__ uint32_t s_scan[kWarps];
+    const uint32_t H = min(cb.cs->hub_count, cb.hub_cap);
+    uint32_t base_run = 0;
+    for (uint32_t b = 0; b < H; b += kThreads) {
+        const uint32_t h = b + threadIdx.x;
+        const uint32_t v = h < H ? (uint32_t)cb.hubs[h].nch : 0u;
+        uint32_t tot;
+        const uint32_t x = block_excl_scan(v, s_scan, tot);
+        if (h < H) cb.chunk_off[h] = base_run + x;
+        base_run += tot;
+    }
+    if (threadIdx.x == 0) {
+        cb.chunk_off[H] = base_run;
+        cb.cs->hub_chunks = min(base_run, cb.chunk_cap);
+        cb.cs->hub_count = H;
+    }
+}
+
+__device__ __forceinline__ int find_hub(const uint32_t *off, int H, uint32_t item) {
+    int lo = 0, hi = H;  // largest h with off[h] <= item
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldcg(off + mid) <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Work-stealing loop shared by k_wdeg and k_spmm: items [0, hub_chunks) are hub chunks,
+// the next c.items are blocks of light rows.
+struct ItemRef {
+    int kind;   // 0 = hub chunk, 1 = light rows, -1 = done
+    int local;  // chunk index within hub / row block within graph
+    int hub;    // hub entry
+};
+
+__device__ __forceinline__ ItemRef next_item(const Ctx &c, int ctr, int *s_it, uint32_t hub_chunks, int H) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_it = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
+    __syncthreads();
+    const uint32_t it = (uint32_t)*s_it;
+    ItemRef r;
+    r.hub = -1;
+    if (it < hub_chunks) {
+        r.kind = 0;
+        r.hub = find_hub(c.cb.chunk_off, H, it);
+        r.local = (int)(it - __ldcg(c.cb.chunk_off + r.hub));
+    } else if (it - hub_chunks < (uint32_t)c.items) {
+        r.kind = 1;
+        r.local = (int)(it - hub_chunks);
+    } else {
+        r.kind = -1;
+        r.local = 0;
+    }
+    return r;
+}
+
+// clamp a CSR row range to [0, E] (only matters after a reported failure)
+__device__ __forceinline__ void row_range(const GraphDesc &g, int64_t row, int64_t &s, int64_t &e) {
+    s = __ldcg(g.rowptr + row);
+    e = __ldcg(g.rowptr + row + 1);
+    s = min(max(s, (int64_t)0), g.E);
+    e = min(max(e, s), g.E);
+}
+
+// ------------------------------------------------------------------------------------
+// k_wdeg: D_ii = sum_j e_ij (+1) for weighted graphs, then D^-1/2 and the node table
+
+__device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
+    float t = s + v;
+    if (fabsf(s) >= fabsf(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ int s_it;
+    __shared__ double s_red[kThreads];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
+    const int H = (int)__ldcg(&c.cb.cs->hub_count);
+    for (;;) {
+        ItemRef r = next_item(c, 3, &s_it, hub_chunks, H);
+        if (r.kind < 0) break;
+        if (r.kind == 0) {
+            const HubEntry he = c.cb.hubs[r.hub];
+            load_desc_idx(c, he.g, &sg);
+            if (!sg.wdeg) continue;  // degree and node table already written by k_rowscan
+            int64_t rs, re;
+            row_range(sg, he.row, rs, re);
+            const int64_t cs = rs + (int64_t)r.local * sg.hub_C;
+            const int64_t ce = min(re, cs + sg.hub_C);
+            float s = 0.f, cc = 0.f;
+            for (int64_t e = cs + tid; e < ce; e += kThreads) neumaier_add(s, cc, ld_stream(sg.val + e));
+            s_red[tid] = (double)s + (double)cc;  // FP64 for the heavy-row reduction
+            __syncthreads();
+            for (int o = kThreads / 2; o > 0; o >>= 1) {
+                if (tid < o) s_red[tid] += s_red[tid + o];
+                __syncthreads();
+            }
+            if (tid == 0) {
+                const uint32_t slot = __ldcg(c.cb.chunk_off + r.hub) + (uint32_t)r.local;
+                if (slot < c.cb.chunk_cap) c.cb.part_deg[slot] = s_red[0];
+                __threadfence();
+                const uint32_t arrived = atomicAdd(c.cb.arrive_deg + r.hub, 1u);
+                s_last = (arrived == (uint32_t)he.nch - 1u);
+            }
+            __syncthreads();
+            if (s_last && tid == 0) {
+                __threadfence();
+                const uint32_t off = __ldcg(c.cb.chunk_off + r.hub);
+                double tot = 0.0;
+                for (int k = 0; k < he.nch; ++k)
+                    if (off + k < c.cb.chunk_cap) tot += __ldcg(c.cb.part_deg + off + k);
+                const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
+                write_node(sg, he.row, (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
+            }
+        } else {
+            const int t = load_desc(c, r.local, &sg, sl, c.prefix);
+            if (!sg.wdeg) continue;
+            const int lpr = 1 << sg.lpr_log2;
+            const int gpw = 32 >> sg.lpr_log2;         // row groups per warp
+            const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
+            const int64_t row = (int64_t)t * sg.rows_per_item + warp * gpw + grp;
+            float s = 0.f, cc = 0.f;
+            bool active = false;
+            if (row < sg.N) {
+                int64_t rs, re;
+                row_range(sg, row, rs, re);
+                if (re - rs <= sg.hub_C) {
+                    active = true;
+                    for (int64_t e = rs + gl; e < re; e += lpr) neumaier_add(s, cc, ld_stream(sg.val + e));
+                }
+            }
+            // deterministic tree over the group, result broadcast from the group's lane 0
+            for (int o = lpr >> 1; o > 0; o >>= 1) {
+                const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+                const float c2 = __shfl_down_sync(0xffffffffu, cc, o);
+                if (gl < o) {
+                    float e;
+                    const float t2 = two_sum(s, s2, e);
+                    s = t2;
+                    cc = cc + (c2 + e);
+                }
+            }
+            if (active && gl == 0) {
+                const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
+                write_node(sg, row, (s + cc) + aug, (sg.flags & kOptLap) != 0);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// k_spmm: label-gather product + fused epilogue
+
+// Accumulate val_ij * s_j into per-lane accumulators for the entries [lo, hi) of a row,
+// this lane being lane `gl` of a group of `gsz` lanes.  Vector loads of 4 entries from
+// 16-byte aligned addresses (col/val are padded by 4 entries at the end).
+template <int KR>
+__device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
+                                        float (&acc)[KR], uint32_t &err) {
+    const int64_t a0 = lo & ~(int64_t)3;
+    const bool has_w = g.val != nullptr && g.w != nullptr;
+    const uint32_t N = (uint32_t)g.N;
+    const int64_t step = 4 * (int64_t)gsz;
+    for (int64_t b = a0 + 4 * gl; b < hi; b += 2 * step) {
+        const int64_t b2 = b + step;
+        const bool two = b2 < hi;
+        const int4 c0 = ld_stream4(g.col + b);
+        const float4 v0 = has_w ? ld_stream4(g.val + b) : make_float4(1.f, 1.f, 1.f, 1.f);
+        int4 c1 = make_int4(0, 0, 0, 0);
+        float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (two) {
+            c1 = ld_stream4(g.col + b2);
+            v1 = has_w ? ld_stream4(g.val + b2) : make_float4(1.f, 1.f, 1.f, 1.f);
+        }
+        const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t e = (q < 4 ? b : b2) + (q & 3);
+            if (e >= lo && e < hi && (q < 4 || two)) {
+                uint32_t j = (uint32_t)cc[q];
+                if (j >= N) { err |= kStTimeout; continue; }
+                const int2 t = __ldg(g.tab + j);
+                const float p = vv[q] * __int_as_float(t.y);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) acc[k] += (t.x == k) ? p : 0.0f;
+            }
+        }
+    }
+}
+
+// Same, into a per-warp shared-memory accumulator sacc[k * 32 + lane] (K up to 64).
+__device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
+                                         float *sacc, int lane, uint32_t &err) {
+    const int64_t a0 = lo & ~(int64_t)3;
+    const bool has_w = g.val != nullptr && g.w != nullptr;
+    const uint32_t N = (uint32_t)g.N;
+    const int64_t step = 4 * (int64_t)gsz;
+    for (int64_t b = a0 + 4 * gl; b < hi; b += 2 * step) {
+        const int64_t b2 = b + step;
+        const bool two = b2 < hi;
+        const int4 c0 = ld_stream4(g.col + b);
+        const float4 v0 = has_w ? ld_stream4(g.val + b) : make_float4(1.f, 1.f, 1.f, 1.f);
+        int4 c1 = make_int4(0, 0, 0, 0);
+        float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (two) {
+            c1 = ld_stream4(g.col + b2);
+            v1 = has_w ? ld_stream4(g.val + b2) : make_float4(1.f, 1.f, 1.f, 1.f);
+        }
+        const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t e = (q < 4 ? b : b2) + (q & 3);
+            if (e >= lo && e < hi && (q < 4 || two)) {
+                uint32_t j = (uint32_t)cc[q];
+                if (j >= N) { err |= kStTimeout; continue; }
+                const int2 t = __ldg(g.tab + j);
+                sacc[t.x * 32 + lane] += vv[q] * __int_as_float(t.y);
+            }
+        }
+    }
+}
+
+// Epilogue for one row given its class totals: augmentation term, D_ii^-1/2, row 2-norm.
+// `get(k)` returns the total of class k (k < K); writes Z[row][k] for k = first, first+stride...
+struct RowTail {
+    float dv;     // D_ii^-1/2 (1 without the Laplacian)
+    int yi;       // class of the row's node (0 if unlabelled; then si = 0)
+    float si;     // s_i = D_ii^-1/2 / n_{y_i}
+    bool aug, lap, cor;
+};
+
+__device__ __forceinline__ RowTail row_tail(const GraphDesc &g, int64_t row) {
+    RowTail rt;
+    const int2 ti = __ldg(g.tab + row);
+    rt.yi = ti.x;
+    rt.si = __int_as_float(ti.y);
+    rt.aug = (g.flags & kOptAug) != 0;
+    rt.lap = (g.flags & kOptLap) != 0;
+    rt.cor = (g.flags & kOptCor) != 0;
+    rt.dv = rt.lap ? __ldg(g.dinv + row) : 1.0f;
+    return rt;
+}
+
+__device__ __forceinline__ float finish_entry(float total, int k, const RowTail &rt) {
+    float v = total;
+    if (rt.aug && k == rt.yi) v += rt.si;
+    if (rt.lap) v *= rt.dv;
+    return v;
+}
+
+constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
+
+template <int KR>
+__device__ __forceinline__ void light_rows_reg(const GraphDesc &g, int t, int lane, int warp, uint32_t &err) {
+    const int lpr = 1 << g.lpr_log2;
+    const int gpw = 32 >> g.lpr_log2;
+    const int grp = lane >> g.lpr_log2, gl = lane & (lpr - 1);
+    const int64_t row = (int64_t)t * g.rows_per_item + warp * gpw + grp;
+    float acc[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
+    bool active = false;
+    if (row < g.N) {
+        int64_t rs, re;
+        row_range(g, row, rs, re);
+        if (re - rs <= g.hub_C) {
+            active = true;
+            acc_reg<KR>(g, rs, re, gl, lpr, acc, err);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+        for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (!active) return;
+    const RowTail rt = row_tail(g, row);
+    const int K = g.K;
+    float ss = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        acc[k] = (k < K) ? finish_entry(acc[k], k, rt) : 0.0f;
+        ss += acc[k] * acc[k];
+    }
+    float r = 1.0f;
+    bool div = false;
+    if (rt.cor) {
+        r = sqrtf(ss);
+        div = r > 0.0f;
+    }
+    float *z = g.Z + row * (int64_t)K;
+    for (int k = gl; k < K; k += lpr) {
+        float v = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < KR; ++kk) v = (kk == k) ? acc[kk] : v;
+        z[k] = div ? v / r : v;
+    }
+}
+
+__device__ __forceinline__ void light_rows_smem(const GraphDesc &g, int t, int lane, int warp, float *sacc,
+                                                uint32_t &err) {
+    const int lpr = 1 << g.lpr_log2;
+    const int gpw = 32 >> g.lpr_log2;
+    const int grp = lane >> g.lpr_log2, gl = lane & (lpr - 1);
+    const int64_t row = (int64_t)t * g.rows_per_item + warp * gpw + grp;
+    const int K = g.K;
+    for (int k = 0; k < K; ++k) sacc[k * 32 + lane] = 0.0f;
+    bool active = false;
+    if (row < g.N) {
+        int64_t rs, re;
+        row_range(g, row, rs, re);
+        if (re - rs <= g.hub_C) {
+            active = true;
+            acc_smem(g, rs, re, gl, lpr, sacc, lane, err);
+        }
+    }
+    __syncwarp();
+    const int g0 = grp * lpr;
+    RowTail rt;
+    if (active) rt = row_tail(g, row);
+    // lane gl of the group finalises classes k = gl, gl + lpr, ...
+    float ss = 0.0f;
+    for (int k = gl; k < K; k += lpr) {
+        float tot = 0.0f;
+        for (int j = 0; j < lpr; ++j) tot += sacc[k * 32 + g0 + j];
+        if (active) tot = finish_entry(tot, k, rt);
+        ss += tot * tot;
+        sacc[k * 32 + g0] = tot;  // keep the finished value (slot of the group's lane 0)
+    }
+    // row 2-norm: sum over the group's lanes in a fixed order
+    for (int o = lpr >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    __syncwarp();
+    if (!active) return;
+    float r = 1.0f;
+    bool div = false;
+    if (rt.cor) {
+        r = sqrtf(ss);
+        div = r > 0.0f;
+    }
+    float *z = g.Z + row * (int64_t)K;
+    for (int k = gl; k < K; k += lpr) {
+        const float v = sacc[k * 32 + g0];
+        z[k] = div ? v / r : v;
+    }
+}
+
+// One chunk of a hub row, processed by the whole CTA; the last CTA of the row merges.
+template <int KR>
+__device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, int hub, int chunk, float *sacc,
+                          float *wtot, int *s_last, uint32_t &err) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = g.K;
+    int64_t rs, re;
+    row_range(g, he.row, rs, re);
+    const int64_t cs = rs + (int64_t)chunk * g.hub_C;
+    const int64_t ce = min(re, cs + g.hub_C);
+    // split the chunk into 8 contiguous warp ranges (multiples of 4 entries)
+    const int64_t span = ((ce - cs + kWarps - 1) / kWarps + 3) & ~(int64_t)3;
+    const int64_t ws = min(ce, cs + warp * span), we = min(ce, ws + span);
+    if constexpr (KR > 0) {
+        float acc[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
+        if (ws < we) acc_reg<KR>(g, ws, we, lane, 32, acc, err);
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < KR; ++k)
+                if (k < K) wtot[warp * kMaxK + k] = acc[k];
+    } else {
+        float *wa = sacc + warp * kMaxK * 32;
+        for (int k = 0; k < K; ++k) wa[k * 32 + lane] = 0.0f;
+        __syncwarp();
+        if (ws < we) acc_smem(g, ws, we, lane, 32, wa, lane, err);
+        __syncwarp();
+        for (int k = lane; k < K; k += 32) {
+            float tot = 0.0f;
+            for (int j = 0; j < 32; ++j) tot += wa[k * 32 + j];
+            wtot[warp * kMaxK + k] = tot;
+        }
+    }
+    __syncthreads();
+    // combine the warps with two-sum, publish the chunk partial (sum, compensation)
+    const uint32_t off = __ldcg(c.cb.chunk_off + hub);
+    if (tid < K) {
+        float s = wtot[tid], comp = 0.0f;
+        for (int w = 1; w < kWarps; ++w) {
+            float e;
+            s = two_sum(s, wtot[w * kMaxK + tid], e);
+            comp += e;
+        }
+        const uint32_t slot = off + (uint32_t)chunk;
+        if (slot < c.cb.chunk_cap) c.cb.part_z[(size_t)slot * c.cb.kmax + tid] = make_float2(s, comp);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t arrived = atomicAdd(c.cb.arrive_z + hub, 1u);
+        *s_last = (arrived == (uint32_t)he.nch - 1u);
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    // last chunk to finish: merge all chunks of the row in chunk order
+    const RowTail rt = row_tail(g, he.row);
+    if (tid < K) {
+        float S = 0.0f, C = 0.0f;
+        for (int ch = 0; ch < he.nch; ++ch) {
+            const uint32_t slot = off + (uint32_t)ch;
+            if (slot >= c.cb.chunk_cap) break;
+            const float2 p = __ldcg(c.cb.part_z + (size_t)slot * c.cb.kmax + tid);
+            float e;
+            S = two_sum(S, p.x, e);
+            C += e + p.y;
+        }
+        wtot[tid] = finish_entry(S + C, tid, rt);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float ss = 0.0f;
+        for (int k = 0; k < K; ++k) ss += wtot[k] * wtot[k];
+        wtot[kMaxK * kWarps - 1] = ss;
+    }
+    __syncthreads();
+    if (tid < K) {
+        const float ss = wtot[kMaxK * kWarps - 1];
+        float v = wtot[tid];
+        if (rt.cor) {
+            const float r = sqrtf(ss);
+            if (r > 0.0f) v = v / r;
+        }
+        g.Z[(int64_t)he.row * K + tid] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
+    extern __shared__ __align__(16) float sacc_all[];
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ int s_it;
+    __shared__ int s_last;
+    __shared__ float wtot[kWarps * kMaxK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
+    const int H = (int)__ldcg(&c.cb.cs->hub_count);
+    uint32_t err = 0;
+    for (;;) {
+        ItemRef r = next_item(c, 4, &s_it, hub_chunks, H);
+        if (r.kind < 0) break;
+        if (r.kind == 0) {
+            const HubEntry he = c.cb.hubs[r.hub];
+            load_desc_idx(c, he.g, &sg);
+            const int K = sg.K;
+            if (K <= 1) hub_chunk<1>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
+            else if (K <= 2) hub_chunk<2>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
+            else if (K <= 4) hub_chunk<4>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
+            else if (K <= 8) hub_chunk<8>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
+            else hub_chunk<0>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
+        } else {
+            const int t = load_desc(c, r.local, &sg, sl, c.prefix);
+            const int K = sg.K;
+            if (K <= 1) light_rows_reg<1>(sg, t, lane, warp, err);
+            else if (K <= 2) light_rows_reg<2>(sg, t, lane, warp, err);
+            else if (K <= 4) light_rows_reg<4>(sg, t, lane, warp, err);
+            else if (K <= 8) light_rows_reg<8>(sg, t, lane, warp, err);
+            else light_rows_smem(sg, t, lane, warp, sacc_all + warp * kMaxK * 32, err);
+        }
+        if (err) {
+            atomicOr(sg.status, err);
+            err = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// k_class_counts: C[i][k] = #{entries of row i whose column has label k}; warp per row
+
+constexpr int kCcWarps = 4;  // 4 warps x 64 classes x 32 lanes x 4 B = 32 KB of shared memory
+
+__global__ void __launch_bounds__(kCcWarps * 32) k_class_counts(const int32_t *rowptr, const int32_t *col,
+                                                                int32_t N, const int32_t *y, int32_t K,
+                                                                int32_t *C) {
+    __shared__ int32_t cnt[kCcWarps][kMaxK * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *mine = cnt[warp];
+    for (int64_t row = (int64_t)blockIdx.x * kCcWarps + warp; row < N; row += (int64_t)gridDim.x * kCcWarps) {
+        for (int k = 0; k < K; ++k) mine[k * 32 + lane] = 0;
+        const int64_t s = rowptr[row], e = rowptr[row + 1];
+        for (int64_t p = s + lane; p < e; p += 32) {
+            const int32_t j = col[p];
+            if (j < 0 || j >= N) continue;
+            const int32_t yk = y[j];
+            if (yk >= 0 && yk < K) mine[yk * 32 + lane] += 1;
+        }
+        __syncwarp();
+        for (int k = lane; k < K; k += 32) {
+            int32_t tot = 0;
+            for (int j = 0; j < 32; ++j) tot += mine[k * 32 + j];
+            C[row * K + k] = tot;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_fill(float *p, int64_t n, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// ------------------------------------------------------------------------------------
+// host-side launchers (used by gee_api.cu)
+
+cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)min64((n + kThreads - 1) / kThreads, 4096);
+    k_fill<<<blocks, kThreads, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_prep<<<blocks, kThreads, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const Ctx &c, int blocks, bool final_pass, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    if (final_pass) {
+        k_sort<true><<<blocks, kThreads, kSortSmem, st>>>(c);
+    } else {
+        k_sort<false><<<blocks, kThreads, kSortSmem, st>>>(c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_rowscan<<<blocks, kThreads, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st) {
+    k_hubprep<<<1, kThreads, 0, st>>>(cb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_wdeg<<<blocks, kThreads, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_spmm<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32_t N, const int32_t *y, int32_t K,
+                                int32_t *C, int blocks, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    k_class_counts<<<blocks, kCcWarps * 32, 0, st>>>(rowptr, col, N, y, K, C);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_sort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_sort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+}
+
+int occupancy_spmm(bool smem_acc) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmm, kThreads, smem_acc ? kSmemAccBytes : 0);
+    return n > 0 ? n : 1;
+}
+
+int occupancy_sort() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sort<true>, kThreads, kSortSmem);
+    return n > 0 ? n : 1;
+}
+
+int occupancy_wdeg() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wdeg, kThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace gee
