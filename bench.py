@@ -57,16 +57,19 @@ def make_graph(name, rank=0):
 # ---- algorithmic bytes per launch of each kernel ("Roofline") ------------
 
 def kernel_bytes(g):
+    """Algorithmic DRAM bytes of one launch of each kernel: every array the kernel must
+    read or write once, nothing for re-reads or L2-resident gathers."""
     E, N, K = g.E, g.N, g.K
     wt = 1 if g.w is not None else 0
     two = (N - 1).bit_length() > 11
     b = {}
-    b["k_prep"] = 4 * E + 4 * N
+    b["k_prep"] = 4 * E + 4 * N                                         # src, labels
     if two:
-        b["k_sort_first"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)      # read COO, write packed
-        b["k_sort_final"] = E * (4 + 4 * wt) + E * (4 + 4 * wt)      # read packed, write CSR
+        b["k_scatter_first"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)   # read src/dst/w, write packed/w
+        b["k_count"] = 4 * E + 4 * N                                  # read packed, row lengths
+        b["k_scatter_final"] = E * (4 + 4 * wt) + E * (4 + 4 * wt)   # read packed/w, write col/val
     else:
-        b["k_sort_final"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)      # read COO, write CSR
+        b["k_scatter_final"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)   # read src/dst/w, write col/val
     b["k_rowscan"] = 4 * N + 4 * (N + 1) + (0 if wt else 4 * N + 16 * N)
     b["k_wdeg"] = 4 * E + 4 * (N + 1) + 4 * N + 16 * N if wt else 0
     b["k_spmm"] = E * (4 + 4 * wt) + 4 * (N + 1) + 8 * N + 4 * N + 4 * N * K
@@ -280,7 +283,7 @@ def gpu_arm(args):
 
 
 def gee_phase_count():
-    return 8
+    return 11
 
 
 def e2e_measure(gee, g, dev, stream, opts, args):

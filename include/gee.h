@@ -117,12 +117,14 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
  * milliseconds, into the HOST array phase_ms[GEE_NUM_PHASES] (-1 for a phase that
  * launched nothing).  For measurement only: the work and the result are those of
  * gee_embed.  Phases, in launch order:
- *   0 workspace memset, 1 k_prep (label counts, checks, digit histograms),
- *   2 k_sort first pass (2-pass graphs), 3 k_sort final pass (writes the CSR),
- *   4 k_rowscan (index_pointers, unweighted degrees), 5 k_hubprep (hub-row chunks),
- *   6 k_wdeg (weighted degrees), 7 k_spmm (Z with the fused epilogue).
+ *   0 workspace memset, 1 k_prep (label counts, checks, first-digit histograms per
+ *   range), 2 k_offsets (first pass), 3 k_scatter first pass (graphs with more than
+ *   2^11 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final
+ *   pass), 6 k_scatter final pass (writes the CSR), 7 k_rowscan (index_pointers,
+ *   unweighted degrees), 8 k_hubprep (hub-row chunks), 9 k_wdeg (weighted degrees),
+ *   10 k_spmm (Z with the fused epilogue).
  */
-#define GEE_NUM_PHASES 8
+#define GEE_NUM_PHASES 11
 int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                     const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
                     void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status,

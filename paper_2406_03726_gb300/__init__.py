@@ -32,8 +32,8 @@ STATUS_LABEL = 2
 STATUS_WEIGHT = 4
 STATUS_TIMEOUT = 8
 
-PHASES = ("memset", "k_prep", "k_sort_first", "k_sort_final", "k_rowscan", "k_hubprep", "k_wdeg",
-          "k_spmm")
+PHASES = ("memset", "k_prep", "k_offsets_first", "k_scatter_first", "k_count", "k_offsets_final",
+          "k_scatter_final", "k_rowscan", "k_hubprep", "k_wdeg", "k_spmm")
 
 MAX_N = 1 << 21
 MAX_E = 1 << 30

@@ -138,3 +138,4 @@ def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_b
                    status=None) -> int:
     return lib().gee_embed_host(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
                                 ptr(workspace), workspace_bytes, stream_handle(stream), ptr(status))
+

@@ -18,7 +18,10 @@
 namespace gee {
 
 cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st);
-cudaError_t launch_sort(const Ctx &c, int blocks, bool final_pass, cudaStream_t st);
+cudaError_t launch_offsets(const Ctx &c, int blocks, bool second, cudaStream_t st);
+cudaError_t launch_scatter(const Ctx &c, int blocks, bool final_pass, int max_digit_bits, cudaStream_t st);
+size_t scatter_smem(int max_digit_bits);
+cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st);
 cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st);
@@ -29,18 +32,18 @@ cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st);
 cudaError_t configure_kernels();
 int occupancy_spmm(bool smem_acc);
 int occupancy_wdeg();
-int occupancy_sort();
 
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kSMs = 152;                   // GB300
+constexpr size_t kSmemPerSM = 228 * 1024;   // shared memory per SM usable by CTAs
 
 struct DeviceInfo {
     bool ready = false;
     int sms = 0;
     int occ_spmm[2] = {1, 1};
     int occ_wdeg = 1;
-    int occ_sort = 1;
 };
 
 std::mutex g_mu;
@@ -57,7 +60,6 @@ int device_info(DeviceInfo &out) {
         d.occ_spmm[0] = occupancy_spmm(false);
         d.occ_spmm[1] = occupancy_spmm(true);
         d.occ_wdeg = occupancy_wdeg();
-        d.occ_sort = occupancy_sort();
         d.ready = true;
     }
     out = d;
@@ -127,6 +129,13 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
     d.rows_per_item = kWarps * (32 >> d.lpr_log2);
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
+    // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
+    // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
+    const int maxbits = std::max(d.fbits, first_bits(d));
+    const int per_sm = std::max<int>(1, std::min<int>(4, (int)(kSmemPerSM / (scatter_smem(maxbits) + 1024))));
+    const int target = kSMs * per_sm;
+    d.range_tiles = std::max<int32_t>(1, (d.tiles_e + target - 1) / target);
+    d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
 }
 
 uint32_t hub_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / ((int64_t)d.hub_C + 1)); }
@@ -137,10 +146,8 @@ void layout_zero(Bump &b, GraphDesc &d) {
     d.status = b.take<uint32_t>(1);
     d.rowcnt = b.take<int32_t>((size_t)d.N);
     d.nk = b.take<int32_t>((size_t)d.K);
-    d.hist_lo = b.take<uint32_t>(d.npass == 2 ? (size_t)1 << d.lbits : 0);
-    d.hist_f = b.take<uint32_t>((size_t)1 << d.fbits);
-    d.lb_a = b.take<uint32_t>(d.npass == 2 ? ((size_t)d.tiles_e << d.lbits) : 0);
-    d.lb_f = b.take<uint32_t>((size_t)d.tiles_e << d.fbits);
+    d.hist1 = b.take<uint32_t>((size_t)1 << first_bits(d));
+    d.hist2 = d.npass == 2 ? b.take<uint32_t>((size_t)1 << d.fbits) : nullptr;
     d.lb_s = b.take<uint32_t>((size_t)d.tiles_n);
 }
 
@@ -150,6 +157,8 @@ void layout_rest(Bump &b, GraphDesc &d, bool weighted) {
     d.val = weighted ? b.take<float>((size_t)d.E + 4) : nullptr;
     d.tmpk = d.npass == 2 ? b.take<uint32_t>((size_t)d.E) : nullptr;
     d.tmpw = (d.npass == 2 && weighted) ? b.take<float>((size_t)d.E) : nullptr;
+    d.cnt1 = b.take<uint32_t>((size_t)d.ranges << first_bits(d));
+    d.cnt2 = d.npass == 2 ? b.take<uint32_t>((size_t)d.ranges << d.fbits) : nullptr;
     d.deg = b.take<float>((size_t)d.N);
     d.dinv = b.take<float>((size_t)d.N);
     d.tab = b.take<int2>((size_t)d.N);
@@ -213,8 +222,21 @@ int cuda_check(cudaError_t e) { return e == cudaSuccess ? GEE_OK : GEE_ERR_CUDA;
         if (_rc != GEE_OK) return _rc; \
     } while (0)
 
-// Phases of one call, in launch order (GEE_PHASE_* in gee.h).
-enum Phase { kPhMemset = 0, kPhPrep, kPhSortA, kPhSortF, kPhRowscan, kPhHubprep, kPhWdeg, kPhSpmm, kNumPhases };
+// Phases of one call, in launch order (the GEE_NUM_PHASES list in gee.h).
+enum Phase {
+    kPhMemset = 0,
+    kPhPrep,
+    kPhOffs1,
+    kPhScat1,
+    kPhCount,
+    kPhOffs2,
+    kPhScatF,
+    kPhRowscan,
+    kPhHubprep,
+    kPhWdeg,
+    kPhSpmm,
+    kNumPhases
+};
 
 // Optional per-phase timing: events[i] is recorded before phase i, events[kNumPhases]
 // after the last one; ran[i] tells whether phase i launched anything.
@@ -228,8 +250,18 @@ inline int mark(PhaseEvents *pe, int ph, cudaStream_t st) {
     return cuda_check(cudaEventRecord(pe->ev[ph], st));
 }
 
-// Enqueue the whole path for one planned graph.
-int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe = nullptr) {
+#define GEE_PHASE(ph, cond, launch)                  \
+    do {                                             \
+        GEE_TRY(mark(pe, ph, st));                   \
+        if (cond) {                                  \
+            GEE_TRY(cuda_check(launch));             \
+            if (pe) pe->ran[ph] = true;              \
+        }                                            \
+    } while (0)
+
+// Enqueue the path for one planned graph: the CSR build, degrees and node table, and
+// (embed) the product with its epilogue.
+int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe, bool embed) {
     const GraphDesc &d = p.d;
     Ctx c;
     std::memset(&c, 0, sizeof(c));
@@ -237,49 +269,34 @@ int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, Phas
     c.G = 1;
     c.cb = p.cb;
     if (pe) std::memset(pe->ran, 0, sizeof(pe->ran));
-    GEE_TRY(mark(pe, kPhMemset, st));
-    GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st)));
-    const int prep_items = (int)((d.E + kPrepTile - 1) / kPrepTile + ((int64_t)d.N + kPrepTile - 1) / kPrepTile);
-    c.items = prep_items;
-    GEE_TRY(mark(pe, kPhPrep, st));
-    GEE_TRY(cuda_check(launch_prep(c, prep_items, st)));
-    if (pe) pe->ran[kPhMemset] = true, pe->ran[kPhPrep] = prep_items > 0;
-    GEE_TRY(mark(pe, kPhSortA, st));
-    const int sort_grid = (int)std::min<int64_t>(d.tiles_e, (int64_t)dev.sms * dev.occ_sort);
-    if (d.tiles_e > 0 && d.npass == 2) {
-        c.items = d.tiles_e;
-        GEE_TRY(cuda_check(launch_sort(c, sort_grid, false, st)));
-        if (pe) pe->ran[kPhSortA] = true;
-    }
-    GEE_TRY(mark(pe, kPhSortF, st));
-    if (d.tiles_e > 0) {
-        c.items = d.tiles_e;
-        GEE_TRY(cuda_check(launch_sort(c, sort_grid, true, st)));
-        if (pe) pe->ran[kPhSortF] = true;
-    }
+    const bool two = d.npass == 2;
+    const int node_tiles = (int)(((int64_t)d.N + kPrepTile - 1) / kPrepTile);
+    const int blk1 = ((1 << first_bits(d)) + 31) / 32, blk2 = ((1 << d.fbits) + 31) / 32;
+    const bool edges = d.ranges > 0;
+    GEE_PHASE(kPhMemset, true, cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st));
+    c.items = d.ranges + node_tiles;
+    GEE_PHASE(kPhPrep, c.items > 0, launch_prep(c, c.items, st));
+    c.items = blk1;
+    GEE_PHASE(kPhOffs1, edges, launch_offsets(c, blk1, false, st));
+    c.items = d.ranges;
+    GEE_PHASE(kPhScat1, edges && two, launch_scatter(c, d.ranges, false, d.lbits, st));
+    GEE_PHASE(kPhCount, edges && two, launch_count(c, d.ranges, st));
+    c.items = blk2;
+    GEE_PHASE(kPhOffs2, edges && two, launch_offsets(c, blk2, true, st));
+    c.items = d.ranges;
+    GEE_PHASE(kPhScatF, edges, launch_scatter(c, d.ranges, true, d.fbits, st));
     c.items = d.tiles_n;
-    GEE_TRY(mark(pe, kPhRowscan, st));
-    GEE_TRY(cuda_check(launch_rowscan(c, d.tiles_n, st)));
-    if (pe) pe->ran[kPhRowscan] = d.tiles_n > 0;
-    GEE_TRY(mark(pe, kPhHubprep, st));
-    if (p.cb.hub_cap > 0) {
-        GEE_TRY(cuda_check(launch_hubprep(p.cb, st)));
-        if (pe) pe->ran[kPhHubprep] = true;
-    }
+    GEE_PHASE(kPhRowscan, d.tiles_n > 0, launch_rowscan(c, d.tiles_n, st));
+    const bool hubs = p.cb.hub_cap > 0 && (embed || d.wdeg);
+    GEE_PHASE(kPhHubprep, hubs, launch_hubprep(p.cb, st));
     const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
     c.items = row_items;
     const int64_t max_items = (int64_t)row_items + (p.cb.hub_cap > 0 ? p.cb.chunk_cap : 0);
-    GEE_TRY(mark(pe, kPhWdeg, st));
-    if (d.wdeg) {
-        const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
-        GEE_TRY(cuda_check(launch_wdeg(c, grid, st)));
-        if (pe) pe->ran[kPhWdeg] = grid > 0;
-    }
+    const int wgrid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
+    GEE_PHASE(kPhWdeg, d.wdeg && wgrid > 0, launch_wdeg(c, wgrid, st));
     const bool smem = d.K > kRegK;
-    const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_spmm[smem ? 1 : 0]);
-    GEE_TRY(mark(pe, kPhSpmm, st));
-    GEE_TRY(cuda_check(launch_spmm(c, grid, smem, st)));
-    if (pe) pe->ran[kPhSpmm] = grid > 0;
+    const int sgrid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_spmm[smem ? 1 : 0]);
+    GEE_PHASE(kPhSpmm, embed && sgrid > 0, launch_spmm(c, sgrid, smem, st));
     GEE_TRY(mark(pe, kNumPhases, st));
     return GEE_OK;
 }
@@ -359,7 +376,7 @@ int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int
     p.d.w = d_w;
     p.d.y = d_labels;
     p.d.Z = d_Z;
-    GEE_TRY(run_single(p, dev, st, pe));
+    GEE_TRY(run_single(p, dev, st, pe, true));
     if (d_status)
         GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
     return GEE_OK;
@@ -428,31 +445,7 @@ int gee_build_csr(const int32_t *d_src, const int32_t *d_dst, const float *d_w, 
     p.d.y = d_labels;
     p.d.Z = nullptr;
     const GraphDesc &d = p.d;
-    Ctx c;
-    std::memset(&c, 0, sizeof(c));
-    c.g0 = d;
-    c.G = 1;
-    c.cb = p.cb;
-    GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st)));
-    const int prep_items = (int)((d.E + kPrepTile - 1) / kPrepTile + ((int64_t)d.N + kPrepTile - 1) / kPrepTile);
-    c.items = prep_items;
-    GEE_TRY(cuda_check(launch_prep(c, prep_items, st)));
-    if (d.tiles_e > 0) {
-        c.items = d.tiles_e;
-        const int sort_grid = (int)std::min<int64_t>(d.tiles_e, (int64_t)dev.sms * dev.occ_sort);
-        if (d.npass == 2) GEE_TRY(cuda_check(launch_sort(c, sort_grid, false, st)));
-        GEE_TRY(cuda_check(launch_sort(c, sort_grid, true, st)));
-    }
-    c.items = d.tiles_n;
-    GEE_TRY(cuda_check(launch_rowscan(c, d.tiles_n, st)));
-    if (d.wdeg) {
-        if (p.cb.hub_cap > 0) GEE_TRY(cuda_check(launch_hubprep(p.cb, st)));
-        const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
-        c.items = row_items;
-        const int64_t max_items = (int64_t)row_items + (p.cb.hub_cap > 0 ? p.cb.chunk_cap : 0);
-        const int grid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
-        GEE_TRY(cuda_check(launch_wdeg(c, grid, st)));
-    }
+    GEE_TRY(run_single(p, dev, st, nullptr, false));
     GEE_TRY(cuda_check(cudaMemcpyAsync(d_rowptr, d.rowptr, sizeof(int32_t) * ((size_t)N + 1),
                                        cudaMemcpyDeviceToDevice, st)));
     if (E > 0) {

@@ -15,8 +15,8 @@ namespace gee {
 // ---- tile geometry --------------------------------------------------------------------
 constexpr int kThreads = 256;                  // every kernel uses 256-thread CTAs
 constexpr int kWarps = kThreads / 32;
-constexpr int kSortItems = 16;                 // keys per thread in a sort pass
-constexpr int kSortTile = kThreads * kSortItems;   // 4096 edges per sort tile
+constexpr int kSortItems = 8;                  // keys per thread in a sort pass
+constexpr int kSortTile = kThreads * kSortItems;   // 2048 edges per sort tile
 constexpr int kPrepTile = 8192;                // edges (or nodes) per histogram tile
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kThreads * kScanItems;   // 4096 nodes per scan tile
@@ -57,6 +57,8 @@ struct GraphDesc {
     int32_t tiles_n;         // ceil(N / kScanTile)
     int32_t rows_per_item;   // light rows per SpMM work item
     int32_t wdeg;            // 1: degrees and node table come from k_wdeg (weighted + Laplacian)
+    int32_t range_tiles;     // sort tiles per range; one CTA scatters one range
+    int32_t ranges;          // ceil(tiles_e / range_tiles)
     // scratch (device)
     int32_t *rowptr;         // [N+1]
     int32_t *rowcnt;         // [N]           zeroed
@@ -64,10 +66,10 @@ struct GraphDesc {
     float *val;              // [E + 4]       weighted only
     uint32_t *tmpk;          // [E]           2-pass: (src >> lbits) << nbits | dst
     float *tmpw;             // [E]           2-pass weighted
-    uint32_t *hist_lo;       // [2^lbits]     zeroed
-    uint32_t *hist_f;        // [2^fbits]     zeroed
-    uint32_t *lb_a;          // [tiles_e << lbits] zeroed
-    uint32_t *lb_f;          // [tiles_e << fbits] zeroed
+    uint32_t *hist1;         // [2^b1]        zeroed: first-pass digit totals (b1 = lbits, or fbits for 1 pass)
+    uint32_t *hist2;         // [2^fbits]     zeroed: final-pass digit totals (2-pass graphs)
+    uint32_t *cnt1;          // [ranges << b1]    per-range first-pass digit counts, then bucket offsets
+    uint32_t *cnt2;          // [ranges << fbits] per-range final-pass digit counts, then offsets (2-pass)
     uint32_t *lb_s;          // [tiles_n]     zeroed
     int32_t *nk;             // [K]           zeroed
     float *deg;              // [N]  D_ii
@@ -75,6 +77,8 @@ struct GraphDesc {
     int2 *tab;               // [N]  {class or 0, s_j as float bits (0 if unlabelled)}
     uint32_t *status;        // [1]           zeroed
 };
+
+__host__ __device__ inline int first_bits(const GraphDesc &g) { return g.npass == 2 ? g.lbits : g.fbits; }
 
 // Per-call state shared by all graphs of a launch sequence (zeroed at the start).
 struct CallState {
@@ -112,6 +116,17 @@ struct Ctx {
 };
 
 // item prefixes stored per kernel for batched calls
-enum PrefixKind { kPfxPrep = 0, kPfxSortA = 1, kPfxSortF = 2, kPfxScan = 3, kPfxRows = 4, kPfxWRows = 5, kNumPfx = 6 };
+enum PrefixKind {
+    kPfxPrep = 0,     // ranges + node tiles
+    kPfxOffs1 = 1,    // 32-digit blocks of the first pass
+    kPfxScat1 = 2,    // ranges of 2-pass graphs (first pass)
+    kPfxCount = 3,    // ranges of 2-pass graphs (final-pass counts)
+    kPfxOffs2 = 4,    // 32-digit blocks of the final pass (2-pass graphs)
+    kPfxScatF = 5,    // ranges (final pass)
+    kPfxScan = 6,     // node tiles of the row scan
+    kPfxRows = 7,     // light-row items of the SpMM
+    kPfxWRows = 8,    // light-row items of the weighted-degree kernel
+    kNumPfx = 9
+};
 
 }  // namespace gee

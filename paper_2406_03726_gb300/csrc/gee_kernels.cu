@@ -1,10 +1,13 @@
 // Device kernels of the sparse GEE path (Qin & Shen, Section 2 Eq. 1, Table 1, Section 3).
 //
-//   k_prep     label counts n_k (definition of W), input checks, radix-digit histograms of
-//              the source ids
-//   k_sort     one stable LSD radix pass over the edges, keyed by source id, tile by tile
-//              with decoupled look-back; the final pass writes the CSR (col_indices, data)
-//              and the row lengths
+//   k_prep     label counts n_k (definition of W), input checks, per-range histograms of
+//              the first radix digit of the source ids
+//   k_offsets  per-range bucket offsets of a radix pass (prefix over digits and ranges)
+//   k_scatter  one stable LSD radix pass over the edges, keyed by source id, one CTA per
+//              range with TMA-staged tiles; the final pass writes the CSR (col_indices,
+//              data)
+//   k_count    (graphs with more than 2^11 nodes) final-digit histograms of the packed
+//              first-pass output and the row lengths
 //   k_rowscan  index_pointers by a look-back scan of the row lengths; unweighted degrees
 //              D_ii and the node table s_j = D_jj^-1/2 / n_{y_j}; hub-row list
 //   k_hubprep  chunk offsets of the split (hub) rows
@@ -15,7 +18,7 @@
 //              fused into the epilogue; hub rows are split across CTAs and merged with
 //              two-sum compensation by the last CTA to finish
 //
-// Every inter-CTA wait is bounded (kSpinLimit) and records kStTimeout instead of hanging;
+// Every inter-CTA or copy wait is bounded (kSpinLimit) and records kStTimeout instead of hanging;
 // every global index derived from data is range-checked, so bad input cannot make a
 // kernel touch memory outside its buffers.
 #include "gee_internal.cuh"
@@ -135,28 +138,6 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     return before + x - v;
 }
 
-// Decoupled look-back over the tiles before `t` for one bucket: the sum of their counts.
-__device__ __forceinline__ uint32_t look_back(const uint32_t *lb, int width, int t, int d, uint32_t &err) {
-    uint32_t excl = 0;
-    int j = t - 1, spins = 0;
-    while (j >= 0) {
-        uint32_t s = ld_relaxed(lb + (size_t)j * width + d);
-        uint32_t f = s & ~kValMask;
-        if (f == 0u) {
-            if (++spins > kSpinLimit) {
-                err |= kStTimeout;
-                break;
-            }
-            if (spins > 64) __nanosleep(128);
-            continue;
-        }
-        excl += s & kValMask;
-        if (f == kFlagPre) break;
-        --j;
-    }
-    return excl;
-}
-
 // Error-free transformation: s + e == a + b exactly (Knuth's two-sum).
 __device__ __forceinline__ float two_sum(float a, float b, float &e) {
     float s = a + b;
@@ -170,104 +151,174 @@ __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) &
 // ------------------------------------------------------------------------------------
 // k_prep: histograms of source-id digits (edge tiles), class sizes n_k (node tiles)
 
+// ------------------------------------------------------------------------------------
+// CSR build: stable LSD radix sort of the edges by source id (Section 3 CSR, rows in
+// input order).  A graph's edges are cut into ranges of range_tiles x 4096 edges.
+//
+//   k_prep       per range: histogram of the first-pass digit of the source ids
+//                (low lbits for 2-pass graphs, the whole id for graphs with <= 2^11
+//                nodes); per node tile: class sizes n_k and label checks
+//   k_offsets    per digit: exclusive prefix over (digit, range) -> the bucket offset
+//                at which each range starts writing each digit
+//   k_scatter    one CTA per range scatters its tiles in order from those offsets:
+//                first pass -> packed ((src >> lbits) << nbits | dst) + weight,
+//                final pass -> col / val of the CSR
+//   k_count      (2-pass graphs) per range of the packed array: histogram of the
+//                final-pass digit, and the exact row lengths rowcnt
+// No CTA ever waits for another: the offsets are known before a range is scattered.
+
 constexpr int kPrivDigits = 512;  // digit counts up to this get one private histogram per warp
+
+__device__ __forceinline__ int64_t range_begin(const GraphDesc &g, int r) {
+    return (int64_t)r * g.range_tiles * kSortTile;
+}
+__device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
+    return (int)min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
+}
+
+// Stream the ids [0, n) of p (16-byte vectors when aligned) through f(value).
+template <class F>
+__device__ __forceinline__ void stream_ids(const int32_t *p, int n, F &&f) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+        constexpr int kV = 8;
+        const int nv = n >> 2;
+        for (int base = 0; base < nv; base += kV * kThreads) {
+            int4 v[kV];
+#pragma unroll
+            for (int k = 0; k < kV; ++k) {
+                const int vi = base + threadIdx.x + k * kThreads;
+                v[k] = vi < nv ? ld_stream4(p + 4 * vi) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kV; ++k) {
+                if (base + (int)threadIdx.x + k * kThreads < nv) {
+                    f(v[k].x);
+                    f(v[k].y);
+                    f(v[k].z);
+                    f(v[k].w);
+                }
+            }
+        }
+        if ((int)threadIdx.x < n - 4 * nv) f(ld_stream(p + 4 * nv + threadIdx.x));
+    } else {
+        for (int i = threadIdx.x; i < n; i += kThreads) f(ld_stream(p + i));
+    }
+}
 
 __global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
-    __shared__ uint32_t h_lo[kWarps * kPrivDigits];
-    __shared__ uint32_t h_f[kWarps * kPrivDigits];
+    __shared__ uint32_t h[kWarps * kPrivDigits];
     __shared__ uint32_t s_err;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     if (tid == 0) s_err = 0;
     uint32_t err = 0;
-    const int64_t tiles_p = (sg.E + kPrepTile - 1) / kPrepTile;
-    if (t < tiles_p) {
-        const bool two = sg.npass == 2;
-        const int Dl = two ? (1 << sg.lbits) : 0, Df = 1 << sg.fbits;
-        // private per-warp histograms when they fit, one shared histogram otherwise
-        const int strl = (Dl <= kPrivDigits) ? Dl : 0, strf = (Df <= kPrivDigits) ? Df : 0;
-        const int nl = strl ? kWarps * Dl : Dl, nf = strf ? kWarps * Df : Df;
-        for (int i = tid; i < nf; i += kThreads) h_f[i] = 0;
-        for (int i = tid; i < nl; i += kThreads) h_lo[i] = 0;
+    if (t < sg.ranges) {
+        const int b1 = first_bits(sg);
+        const int D = 1 << b1;
+        const int str = (D <= kPrivDigits) ? D : 0;  // private per-warp histograms when they fit
+        const int nh = str ? kWarps * D : D;
+        for (int i = tid; i < nh; i += kThreads) h[i] = 0;
         __syncthreads();
-        uint32_t *hl = h_lo + warp * strl, *hf = h_f + warp * strf;
-        const int64_t e0 = (int64_t)t * kPrepTile;
-        const int n = (int)min64(kPrepTile, sg.E - e0);
-        const int32_t *s = sg.src + e0;
+        uint32_t *hw = h + warp * str;
         const uint32_t N = (uint32_t)sg.N;
-        const int lb = sg.lbits;
-        const uint32_t lm = (1u << lb) - 1u;
-        auto add = [&](int v) {
+        const uint32_t m = (1u << b1) - 1u;
+        stream_ids(sg.src + range_begin(sg, t), range_len(sg, t), [&](int v) {
             if ((uint32_t)v >= N) {
                 err |= kStIndex;
                 v = 0;
             }
-            if (two) {
-                atomicAdd(&hl[(uint32_t)v & lm], 1u);
-                atomicAdd(&hf[(uint32_t)v >> lb], 1u);
-            } else {
-                atomicAdd(&hf[v], 1u);
-            }
-        };
-        if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0) {
-            constexpr int kV = kPrepTile / (4 * kThreads);  // 8 vectors of 4 ids per thread
-            const int nv = n >> 2;
-            int4 v[kV];
-#pragma unroll
-            for (int k = 0; k < kV; ++k) {
-                const int vi = tid + k * kThreads;
-                v[k] = vi < nv ? ld_stream4(s + 4 * vi) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kV; ++k) {
-                if (tid + k * kThreads < nv) {
-                    add(v[k].x);
-                    add(v[k].y);
-                    add(v[k].z);
-                    add(v[k].w);
-                }
-            }
-            if (tid < n - 4 * nv) add(ld_stream(s + 4 * nv + tid));
-        } else {
-            for (int i = tid; i < n; i += kThreads) add(ld_stream(s + i));
-        }
+            atomicAdd(&hw[(uint32_t)v & m], 1u);
+        });
         __syncthreads();
-        for (int d = tid; d < Df; d += kThreads) {
+        uint32_t *out = sg.cnt1 + ((size_t)t << b1);
+        for (int d = tid; d < D; d += kThreads) {
             uint32_t v = 0;
-            if (strf)
-                for (int w = 0; w < kWarps; ++w) v += h_f[w * Df + d];
+            if (str)
+                for (int w = 0; w < kWarps; ++w) v += h[w * D + d];
             else
-                v = h_f[d];
-            if (v) atomicAdd(&sg.hist_f[d], v);
-        }
-        for (int d = tid; d < Dl; d += kThreads) {
-            uint32_t v = 0;
-            if (strl)
-                for (int w = 0; w < kWarps; ++w) v += h_lo[w * Dl + d];
-            else
-                v = h_lo[d];
-            if (v) atomicAdd(&sg.hist_lo[d], v);
+                v = h[d];
+            out[d] = v;
+            if (v) atomicAdd(&sg.hist1[d], v);
         }
     } else {
-        const int64_t n0 = (int64_t)(t - tiles_p) * kPrepTile;
+        const int64_t n0 = (int64_t)(t - sg.ranges) * kPrepTile;
         const int n = (int)min64(kPrepTile, (int64_t)sg.N - n0);
         const int K = sg.K;
-        for (int i = tid; i < K; i += kThreads) h_f[i] = 0;
+        for (int i = tid; i < K; i += kThreads) h[i] = 0;
         __syncthreads();
         for (int i = tid; i < n; i += kThreads) {
             int yv = __ldg(sg.y + n0 + i);
             if (yv < -1 || yv >= K) err |= kStLabel;
-            else if (yv >= 0) atomicAdd(&h_f[yv], 1u);
+            else if (yv >= 0) atomicAdd(&h[yv], 1u);
         }
         __syncthreads();
         for (int i = tid; i < K; i += kThreads)
-            if (h_f[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h_f[i]);
+            if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h[i]);
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (tid == 0 && s_err) atomicOr(sg.status, s_err);
+}
+
+// k_offsets: for a block of 32 digits, rewrite cnt[r][d] (counts) as the position where
+// range r writes its first element of digit d: dbase[d] + sum_{r' < r} cnt[r'][d], with
+// dbase the exclusive prefix over digits of the totals.  Warp w owns a slice of ranges.
+template <bool SECOND>
+__global__ void __launch_bounds__(kThreads) k_offsets(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t csum[kWarps][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    const int bits = SECOND ? sg.fbits : first_bits(sg);
+    const int D = 1 << bits;
+    uint32_t *cnt = SECOND ? sg.cnt2 : sg.cnt1;
+    const uint32_t *tot = SECOND ? sg.hist2 : sg.hist1;
+    const int d0 = 32 * b, d = d0 + lane;
+    // prefix of the totals below this digit block
+    uint32_t part = 0;
+    for (int i = tid; i < d0; i += kThreads) part += __ldcg(tot + i);
+    uint32_t below;
+    (void)block_excl_scan(part, s_scan, below);
+    const uint32_t td = d < D ? __ldcg(tot + d) : 0u;
+    uint32_t x = td;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const uint32_t dbase = below + x - td;
+    const int R = sg.ranges;
+    const int chunk = (R + kWarps - 1) / kWarps;
+    const int r0 = min(R, warp * chunk), r1 = min(R, r0 + chunk);
+    uint32_t s = 0;
+    if (d < D) {
+        int r = r0;
+        for (; r + 4 <= r1; r += 4) {
+            const uint32_t a0 = __ldcg(cnt + ((size_t)r << bits) + d);
+            const uint32_t a1 = __ldcg(cnt + ((size_t)(r + 1) << bits) + d);
+            const uint32_t a2 = __ldcg(cnt + ((size_t)(r + 2) << bits) + d);
+            const uint32_t a3 = __ldcg(cnt + ((size_t)(r + 3) << bits) + d);
+            s += a0 + a1 + a2 + a3;
+        }
+        for (; r < r1; ++r) s += __ldcg(cnt + ((size_t)r << bits) + d);
+    }
+    csum[warp][lane] = s;
+    __syncthreads();
+    uint32_t run = dbase;
+    for (int w = 0; w < warp; ++w) run += csum[w][lane];
+    if (d < D) {
+        for (int r = r0; r < r1; ++r) {
+            uint32_t *p = cnt + ((size_t)r << bits) + d;
+            const uint32_t v = __ldcg(p);
+            *p = run;
+            run += v;
+        }
+        if (!SECOND && sg.npass == 1 && warp == 0 && d < sg.N) sg.rowcnt[d] = (int32_t)td;  // digit = row
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -350,47 +401,46 @@ __device__ __forceinline__ uint32_t look_back8(const uint32_t *lb, int width, in
 }
 
 // ------------------------------------------------------------------------------------
-// k_sort: one stable radix pass over the edges of one or many graphs.
+// k_scatter: one CTA scatters one range, tile by tile, in order.
 //
-//   FINAL = false  first of two passes (graphs with more than 2^11 nodes): digit = low
-//                  lbits of the source id; edge list -> packed ((src >> lbits) << nbits |
-//                  dst) + weight, in digit order.
-//   FINAL = true   last pass: 1-pass graphs read the edge list (digit = source id), 2-pass
-//                  graphs read the packed array (digit = high bits); writes col/val at their
-//                  CSR positions and adds each tile's row-run lengths to rowcnt.
+//   FINAL = false  first pass of a 2-pass graph: digit = low lbits of the source id,
+//                  edge list -> packed + weight
+//   FINAL = true   last pass: 1-pass graphs read the edge list (digit = source id) with
+//                  the cnt1 offsets, 2-pass graphs read the packed array (digit = high
+//                  bits) with the cnt2 offsets; writes col / val
 //
-// Persistent CTAs claim 4096-edge tiles in order.  While a tile is ranked and scattered,
-// the next claimed tile streams into shared memory by TMA bulk copies.  Warp w ranks tile
-// elements [512 w, 512 w + 512), item i of lane l being element 512 w + 32 i + l, with
-// match.any in input order, so ranks are stable.  Bucket offsets across tiles come from a
-// decoupled look-back on per-(tile, digit) status words.
+// Tiles of 2048 edges, 8 per thread.  While a tile is ranked and scattered, the next tile
+// of the range streams into shared memory by TMA bulk copies.  Warp w ranks tile
+// elements [256 w, 256 w + 256), item i of lane l being element 256 w + 32 i + l: the
+// lanes holding the same digit are found with one ballot per digit bit (all items at
+// once), then a per-warp counter per digit gives each element its rank among the equal
+// digits before it in input order, so the pass is stable.
+//
+// Shared memory (dynamic, sized by the digit count D): stage (3 streams x 2048 words),
+// a work area (per-warp u16 digit counters + tile starts while ranking, then the tile
+// sorted by digit), and the per-digit output positions and running range offsets.
 
-constexpr int kStreamWords = kSortTile;                         // one stream = 4096 words
-constexpr size_t kStageBytes = (size_t)3 * kStreamWords * 4;     // src|tmpk, dst, w|tmpw
-constexpr size_t kWorkBytes = (size_t)3 * kSortTile * 4;         // union, see below
-constexpr size_t kSortSmem = kStageBytes + kWorkBytes + (size_t)2 * kMaxDigits * 4;
+constexpr int kStreamWords = kSortTile;                       // one stream = 2048 words
+constexpr size_t kStageBytes = (size_t)3 * kStreamWords * 4;  // src|tmpk, dst, w|tmpw
 
-struct SortTileInfo {
-    int t;         // tile index within its graph
-    int g;         // graph index
-    int n;         // edges in the tile
-    int staged;    // 1: the first (n & ~3) edges are in the stage buffers
-};
+__host__ __device__ constexpr size_t scatter_work_bytes(int D) {
+    return ((size_t)D * kWarps * 2 + (size_t)D * 4) > (size_t)3 * kSortTile * 4
+               ? ((size_t)D * kWarps * 2 + (size_t)D * 4)
+               : (size_t)3 * kSortTile * 4;
+}
+__host__ __device__ constexpr size_t scatter_smem_bytes(int D) {
+    return kStageBytes + scatter_work_bytes(D) + (size_t)2 * D * 4;
+}
 
 template <bool FINAL>
-__device__ __forceinline__ void sort_issue_stage(const GraphDesc &g, int t, uint32_t *stage, uint64_t *bar,
-                                                 SortTileInfo &info) {
+__device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e0, int n, uint32_t *stage,
+                                                   uint64_t *bar) {
     const bool coo = !FINAL || g.npass == 1;
-    const int64_t e0 = (int64_t)t * kSortTile;
-    const int n = (int)min64(kSortTile, g.E - e0);
     const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
     const void *p0 = coo ? (const void *)(g.src + e0) : (const void *)(g.tmpk + e0);
     const void *p1 = coo ? (const void *)(g.dst + e0) : nullptr;
     const void *p2 = g.w ? (coo ? (const void *)(g.w + e0) : (const void *)(g.tmpw + e0)) : nullptr;
     const bool ok = bytes > 0 && aligned16(p0) && (!p1 || aligned16(p1)) && (!p2 || aligned16(p2));
-    info.t = t;
-    info.n = n;
-    info.staged = ok ? 1 : 0;
     if (ok) {
         fence_proxy_async();  // earlier generic reads of the stage precede these async writes
         const uint32_t nstreams = 1u + (p1 ? 1u : 0u) + (p2 ? 1u : 0u);
@@ -399,133 +449,71 @@ __device__ __forceinline__ void sort_issue_stage(const GraphDesc &g, int t, uint
         if (p1) bulk_g2s(stage + kStreamWords, p1, bytes, bar);
         if (p2) bulk_g2s(stage + 2 * kStreamWords, p2, bytes, bar);
     }
+    return ok ? 1 : 0;
 }
 
 template <bool FINAL>
-__global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
+__global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
-    unsigned char *work = smem + kStageBytes;
-    // union member 1 (ranking): per-warp digit counters, tile starts, first-pass bases
-    uint16_t *wcnt = reinterpret_cast<uint16_t *>(work);
-    uint32_t *tstart = reinterpret_cast<uint32_t *>(work + (size_t)kWarps * kMaxDigits * 2);
-    uint32_t *lobase = tstart + kMaxDigits;
-    // union member 2 (scatter): the tile sorted by digit
-    uint32_t *skey = reinterpret_cast<uint32_t *>(work);
-    uint32_t *spay = skey + kSortTile;
-    float *sw = reinterpret_cast<float *>(spay + kSortTile);
-    uint32_t *dglob = reinterpret_cast<uint32_t *>(work + kWorkBytes);
-    uint32_t *dbase = dglob + kMaxDigits;
-
-    __shared__ GraphDesc sgd[2];
-    __shared__ SortTileInfo sinfo[2];
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_item;
     __shared__ uint32_t s_scan[kWarps];
     __shared__ uint32_t s_err;
-    __shared__ uint32_t s_lo_first, s_lo_last;
+    __shared__ int s_staged;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ctr = FINAL ? 1 : 0;
-    uint32_t err = 0;
-    bool stage_timeout = false;
+    const int r = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    const bool coo = !FINAL || sg.npass == 1;
+    const int bits = FINAL ? sg.fbits : sg.lbits;
+    const int D = 1 << bits;
+    const int nb = sg.nbits, lb = sg.lbits;
+    const uint32_t nmask = (1u << nb) - 1u;  // nb <= 21
+    const bool has_w = sg.w != nullptr;
+    const bool lap = (sg.flags & kOptLap) != 0;
+    const uint32_t N = (uint32_t)sg.N;
+    const uint32_t E32 = (uint32_t)sg.E;
+    const uint32_t *offs = (FINAL && sg.npass == 2) ? sg.cnt2 : sg.cnt1;
 
-    // resolve work item -> graph descriptor (tid 0 only)
-    auto resolve = [&](int item, int slot) {
-        int g = 0, base = 0;
-        if (c.G > 1) {
-            g = find_graph(c.prefix, c.G, item);
-            base = __ldg(c.prefix + g);
-            sgd[slot] = c.graphs[g];
-        } else {
-            sgd[slot] = c.g0;
-        }
-        sinfo[slot].g = g;
-        sort_issue_stage<FINAL>(sgd[slot], item - base, stage, &bar, sinfo[slot]);
-    };
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    unsigned char *work = smem + kStageBytes;
+    uint16_t *wcnt = reinterpret_cast<uint16_t *>(work);                  // [kWarps][D]
+    uint32_t *tstart = reinterpret_cast<uint32_t *>(work + (size_t)D * kWarps * 2);  // [D]
+    uint32_t *skey = reinterpret_cast<uint32_t *>(work);                  // sorted tile
+    uint32_t *spay = skey + kSortTile;
+    float *sw = reinterpret_cast<float *>(spay + kSortTile);
+    uint32_t *dglob = reinterpret_cast<uint32_t *>(work + scatter_work_bytes(D));  // [D]
+    uint32_t *run = dglob + D;                                            // [D]
+
+    const int dpt = (D + kThreads - 1) / kThreads;
+    const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
+    const int64_t r0 = range_begin(sg, r);
+    const int rn = range_len(sg, r);
+    const int ntiles = (rn + kSortTile - 1) / kSortTile;
+    uint32_t err = 0;
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
         s_err = 0;
-        s_item = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
-        if (s_item < c.items) resolve(s_item, 0);
+        mbar_init(&bar, 1);
+        s_staged = scatter_issue_stage<FINAL>(sg, r0, min(rn, kSortTile), stage, &bar);
     }
-    __syncthreads();
-    if (s_item >= c.items) return;
-
-    int cur = 0;
-    int cached_g = -1;
+    for (int d = dlo; d < dhi; ++d) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
     uint32_t parity = 0;
-    for (;;) {
-        const GraphDesc &sg = sgd[cur];
-        const SortTileInfo info = sinfo[cur];
-        const int t = info.t, n = info.n;
-        const bool coo = !FINAL || sg.npass == 1;
-        const bool final2 = FINAL && sg.npass == 2;
-        const int bits = FINAL ? sg.fbits : sg.lbits;
-        const int D = 1 << bits;
-        const int nb = sg.nbits, lb = sg.lbits;
-        const uint32_t nmask = (1u << nb) - 1u;  // nb <= 21
-        const int64_t e0 = (int64_t)t * kSortTile;
-        const bool has_w = sg.w != nullptr;
-        const bool lap = (sg.flags & kOptLap) != 0;
-        const uint32_t N = (uint32_t)sg.N;
-        uint32_t *lb_st = FINAL ? sg.lb_f : sg.lb_a;
-        const int dpt = (D + kThreads - 1) / kThreads;
-        const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
 
-        // ---- per-graph bucket bases (exclusive scan of the pass histogram), cached
-        if (info.g != cached_g) {
-            const uint32_t *ghist = FINAL ? sg.hist_f : sg.hist_lo;
-            uint32_t loc = 0;
-            for (int d = dlo; d < dhi; ++d) loc += __ldcg(ghist + d);
-            uint32_t tot;
-            uint32_t run = block_excl_scan(loc, s_scan, tot);
-            for (int d = dlo; d < dhi; ++d) {
-                dbase[d] = run;
-                run += __ldcg(ghist + d);
-            }
-            cached_g = info.g;
-        }
-        // ---- zero the counters; bases of the first pass for 2-pass final tiles
+    for (int ti = 0; ti < ntiles; ++ti) {
+        const int64_t e0 = r0 + (int64_t)ti * kSortTile;
+        const int n = min(kSortTile, rn - ti * kSortTile);
+        __syncthreads();  // the previous tile's write-out is done: its sorted buffer is dead
         for (int i = tid; i < kWarps * D; i += kThreads) wcnt[i] = 0;
-        if (final2) {
-            const int Dl = 1 << lb;
-            const int lpt = (Dl + kThreads - 1) / kThreads;
-            const int llo = min(Dl, tid * lpt), lhi = min(Dl, llo + lpt);
-            uint32_t loc = 0;
-            for (int d = llo; d < lhi; ++d) loc += __ldcg(sg.hist_lo + d);
-            uint32_t tot;
-            uint32_t run = block_excl_scan(loc, s_scan, tot);
-            for (int d = llo; d < lhi; ++d) {
-                lobase[d] = run;
-                run += __ldcg(sg.hist_lo + d);
-            }
-            __syncthreads();
-            if (tid < 2) {
-                const uint32_t p = (uint32_t)(e0 + (tid == 0 ? 0 : max(n - 1, 0)));
-                int a = 0, b = Dl;  // largest d with lobase[d] <= p
-                while (b - a > 1) {
-                    const int m = (a + b) >> 1;
-                    if (lobase[m] <= p) a = m;
-                    else b = m;
-                }
-                if (tid == 0) s_lo_first = a;
-                else s_lo_last = a;
-            }
-        }
-        // ---- wait for this tile's stage
-        if (info.staged) {
-            if (!mbar_wait(&bar, parity)) {
-                err |= kStTimeout;
-                stage_timeout = true;
-            }
+        __syncthreads();  // counters zeroed, s_staged of this tile visible
+        const int staged = s_staged;
+        if (staged) {
+            if (!mbar_wait(&bar, parity)) err |= kStTimeout;
             parity ^= 1u;
         }
-        __syncthreads();
 
-        // ---- load the 16 elements of this thread (stage, or global for the tail)
-        const int nst = info.staged ? (n & ~3) : 0;
+        // ---- load the 8 elements of this thread (stage, or global for the tail)
+        const int nst = staged ? (n & ~3) : 0;
         uint32_t key[kSortItems], pay[kSortItems];
         float wv[kSortItems];
         const int wbase = warp * (32 * kSortItems);
@@ -563,8 +551,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
                 }
             }
         } else {
-            const uint32_t lof = s_lo_first, lol = s_lo_last;
-            const int Dl = 1 << lb;
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i) {
                 const int idx = wbase + i * 32 + lane;
@@ -588,49 +574,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
                         hi &= (uint32_t)(D - 1);
                         d = 0;
                     }
-                    uint32_t lo = lof;
-                    if (lol != lof) {
-                        const uint32_t p = (uint32_t)(e0 + idx);
-                        int a = (int)lof, b = min((int)lol + 1, Dl);
-                        while (b - a > 1) {
-                            const int m = (a + b) >> 1;
-                            if (lobase[m] <= p) a = m;
-                            else b = m;
-                        }
-                        lo = (uint32_t)a;
-                    }
+                    key[i] = hi;
                     pay[i] = d;
-                    key[i] = (hi << lb) | lo;
                     wv[i] = x;
                 }
             }
         }
-        __syncthreads();  // stage consumed, counters zeroed
+        __syncthreads();  // stage consumed
 
-        // ---- claim the next tile and start streaming it into the stage
-        if (tid == 0) {
-            s_item = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
-            if (s_item < c.items) resolve(s_item, cur ^ 1);
+        // ---- start streaming the next tile of this range
+        if (tid == 0 && ti + 1 < ntiles)
+            s_staged = scatter_issue_stage<FINAL>(sg, e0 + kSortTile, min(kSortTile, rn - (ti + 1) * kSortTile),
+                                                  stage, &bar);
+
+        // ---- lanes with equal digits: one ballot per digit bit, all items interleaved
+        unsigned peers[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) peers[i] = __ballot_sync(0xffffffffu, key[i] != 0xffffffffu);
+        for (int b = 0; b < bits; ++b) {
+#pragma unroll
+            for (int i = 0; i < kSortItems; ++i) {
+                const bool bit = (key[i] >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers[i] &= bit ? bal : ~bal;
+            }
         }
-
-        // ---- rank within the warp, in input order
-        uint32_t rank[kSortItems];
+        // ---- stable rank within the warp: per-warp counter of each digit, items in order
         const unsigned lt = lanemask_lt();
         uint16_t *mycnt = wcnt + warp * D;
+        uint32_t rank[kSortItems];
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            const bool valid = key[i] != 0xffffffffu;
-            const uint32_t d = valid ? (final2 ? (key[i] >> lb) : key[i]) : 0xffffffffu;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t d = key[i];
+            const bool valid = d != 0xffffffffu;
             const uint32_t before = valid ? (uint32_t)mycnt[d] : 0u;
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) mycnt[d] = (uint16_t)(before + __popc(peers));
+            if (valid && (peers[i] & lt) == 0u) mycnt[d] = (uint16_t)(before + __popc(peers[i]));
             __syncwarp();
-            rank[i] = before + __popc(peers & lt);
+            rank[i] = before + __popc(peers[i] & lt);
         }
         __syncthreads();
 
-        // ---- per digit: warp offsets, tile counts, tile-local starts
+        // ---- per digit: warp offsets, tile counts, tile-local starts, global positions
         uint32_t tcount[8];  // counts of the owned digits (dpt <= 8)
         uint32_t loc = 0;
 #pragma unroll
@@ -638,6 +623,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
             const int d = dlo + j;
             uint32_t sum = 0;
             if (d < dhi) {
+#pragma unroll
                 for (int w = 0; w < kWarps; ++w) {
                     const uint32_t cnt = wcnt[w * D + d];
                     wcnt[w * D + d] = (uint16_t)sum;
@@ -649,33 +635,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
         }
         {
             uint32_t tot;
-            uint32_t run = block_excl_scan(loc, s_scan, tot);
+            uint32_t tr = block_excl_scan(loc, s_scan, tot);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int d = dlo + j;
                 if (d < dhi) {
-                    tstart[d] = run;
-                    run += tcount[j];
+                    tstart[d] = tr;
+                    dglob[d] = run[d] - tr;
+                    run[d] += tcount[j];
+                    tr += tcount[j];
                 }
-            }
-        }
-
-        // ---- decoupled look-back across tiles, per digit
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int d = dlo + j;
-            if (d < dhi) st_relaxed(lb_st + (size_t)t * D + d, (t == 0 ? kFlagPre : kFlagAgg) | tcount[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int d = dlo + j;
-            if (d < dhi) {
-                uint32_t ex = 0;
-                if (t > 0) {
-                    ex = look_back8(lb_st, D, t, d, err);
-                    st_relaxed(lb_st + (size_t)t * D + d, kFlagPre | ((ex + tcount[j]) & kValMask));
-                }
-                dglob[d] = dbase[d] + ex - tstart[d];
             }
         }
         __syncthreads();
@@ -683,10 +652,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
         // ---- tile-local slot of each element (registers), then scatter into shared memory
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            if (key[i] != 0xffffffffu) {
-                const uint32_t d = final2 ? (key[i] >> lb) : key[i];
-                rank[i] += tstart[d] + wcnt[warp * D + d];
-            }
+            if (key[i] != 0xffffffffu) rank[i] += tstart[key[i]] + wcnt[warp * D + key[i]];
         }
         __syncthreads();  // counters dead: the sorted tile reuses their space
 #pragma unroll
@@ -701,11 +667,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
         __syncthreads();
 
         // ---- write out: consecutive sorted slots of one digit go to consecutive addresses
-        const uint32_t E32 = (uint32_t)sg.E;
+#pragma unroll 4
         for (int s = tid; s < n; s += kThreads) {
-            const uint32_t k = skey[s];
-            const uint32_t d = final2 ? (k >> lb) : k;
-            const uint32_t pos = dglob[d] + (uint32_t)s;
+            const uint32_t pos = dglob[skey[s]] + (uint32_t)s;
             if (pos >= E32) {
                 err |= kStTimeout;
                 continue;
@@ -718,44 +682,102 @@ __global__ void __launch_bounds__(kThreads, 2) k_sort(Ctx c) {
                 if (has_w) sg.tmpw[pos] = sw[s];
             }
         }
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
+}
 
-        // ---- row lengths (final pass): runs of equal source id in the sorted tile
-        if (FINAL) {
-            if (!final2) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int d = dlo + j;
-                    if (d < dhi && tcount[j]) atomicAdd(sg.rowcnt + d, (int)tcount[j]);
+// k_count (2-pass graphs): per range of the packed array, the histogram of the final-pass
+// digit (-> cnt2, hist2) and the row lengths.  Positions of the packed array are grouped
+// by first-pass digit lo (bucket bases = the offsets of range 0 in cnt1), so the range
+// splits into segments of constant lo; within a segment the row of an element is
+// (hi << lbits) | lo.
+__global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ uint32_t acc[kMaxDigits];
+    __shared__ uint32_t seg[kMaxDigits];
+    __shared__ int s_lo[2];
+    __shared__ uint32_t s_err;
+    const int tid = threadIdx.x;
+    const int r = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    const int D2 = 1 << sg.fbits, D1 = 1 << sg.lbits;
+    const int nb = sg.nbits, lb = sg.lbits;
+    const int64_t e0 = range_begin(sg, r);
+    const int n = range_len(sg, r);
+    const uint32_t *lobase = sg.cnt1;  // row 0 of the first-pass offsets: the bucket bases
+    uint32_t err = 0;
+    if (tid == 0) s_err = 0;
+    for (int d = tid; d < D2; d += kThreads) acc[d] = 0;
+    if (tid < 2) {
+        const uint32_t p = (uint32_t)(e0 + (tid == 0 ? 0 : n - 1));
+        int a = 0, b = D1;  // largest bucket with base <= p
+        while (b - a > 1) {
+            const int m = (a + b) >> 1;
+            if (__ldcg(lobase + m) <= p) a = m;
+            else b = m;
+        }
+        s_lo[tid] = a;
+    }
+    __syncthreads();
+    const int lof = s_lo[0], lol = s_lo[1];
+    const bool per_segment = (int64_t)(lol - lof + 1) * D2 <= 4 * (int64_t)n;
+    if (per_segment) {
+        for (int l = lof; l <= lol; ++l) {
+            const int64_t ps = max((int64_t)__ldcg(lobase + l), e0);
+            const int64_t pe = min(l + 1 < D1 ? (int64_t)__ldcg(lobase + l + 1) : sg.E, e0 + n);
+            if (pe <= ps) continue;
+            for (int d = tid; d < D2; d += kThreads) seg[d] = 0;
+            __syncthreads();
+            stream_ids(reinterpret_cast<const int32_t *>(sg.tmpk + ps), (int)(pe - ps), [&](int v) {
+                uint32_t hi = (uint32_t)v >> nb;
+                if (hi >= (uint32_t)D2) {
+                    err |= kStTimeout;
+                    hi = 0;
                 }
-            } else {
-                for (int s = tid; s < n; s += kThreads) {
-                    const uint32_t k = skey[s];
-                    if (k >= N) continue;
-                    const bool st = (s == 0) || skey[s - 1] != k;
-                    const bool en = (s == n - 1) || skey[s + 1] != k;
-                    if (st && en) atomicAdd(sg.rowcnt + k, 1);
-                    else {
-                        if (st) atomicAdd(sg.rowcnt + k, -s);
-                        if (en) atomicAdd(sg.rowcnt + k, s + 1);
-                    }
+                atomicAdd(&seg[hi], 1u);
+            });
+            __syncthreads();
+            for (int d = tid; d < D2; d += kThreads) {
+                const uint32_t v = seg[d];
+                if (v) {
+                    acc[d] += v;
+                    const uint32_t row = ((uint32_t)d << lb) | (uint32_t)l;
+                    if (row < (uint32_t)sg.N) atomicAdd(sg.rowcnt + row, (int)v);
                 }
             }
+            __syncthreads();
         }
-        if (err) {
-            atomicOr(&s_err, err);
-            err = 0;
+    } else {  // many tiny buckets: one atomic per edge
+        for (int i = tid; i < n; i += kThreads) {
+            const uint32_t p = (uint32_t)(e0 + i);
+            uint32_t hi = ld_stream(sg.tmpk + p) >> nb;
+            if (hi >= (uint32_t)D2) {
+                err |= kStTimeout;
+                hi = 0;
+            }
+            int a = lof, b = lol + 1;
+            while (b - a > 1) {
+                const int m = (a + b) >> 1;
+                if (__ldcg(lobase + m) <= p) a = m;
+                else b = m;
+            }
+            atomicAdd(&acc[hi], 1u);
+            const uint32_t row = (hi << lb) | (uint32_t)a;
+            if (row < (uint32_t)sg.N) atomicAdd(sg.rowcnt + row, 1);
         }
         __syncthreads();
-        if (tid == 0 && s_err) {
-            atomicOr(sg.status, s_err);
-            s_err = 0;
-        }
-        const bool more = s_item < c.items;
-        __syncthreads();
-        if (!more) break;
-        cur ^= 1;
     }
-    (void)stage_timeout;
+    uint32_t *out = sg.cnt2 + ((size_t)r << sg.fbits);
+    for (int d = tid; d < D2; d += kThreads) {
+        const uint32_t v = acc[d];
+        out[d] = v;
+        if (v) atomicAdd(&sg.hist2[d], v);
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -810,7 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
         uint32_t ex = 0;
         st_relaxed(sg.lb_s + t, (t == 0 ? kFlagPre : kFlagAgg) | tot);
         if (t > 0) {
-            ex = look_back(sg.lb_s, 1, t, 0, err);
+            ex = look_back8(sg.lb_s, 1, t, 0, err);
             st_relaxed(sg.lb_s + t, kFlagPre | ((ex + tot) & kValMask));
         }
         s_excl = ex;
@@ -1390,13 +1412,26 @@ cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const Ctx &c, int blocks, bool final_pass, cudaStream_t st) {
+cudaError_t launch_offsets(const Ctx &c, int blocks, bool second, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    if (final_pass) {
-        k_sort<true><<<blocks, kThreads, kSortSmem, st>>>(c);
-    } else {
-        k_sort<false><<<blocks, kThreads, kSortSmem, st>>>(c);
-    }
+    if (second) k_offsets<true><<<blocks, kThreads, 0, st>>>(c);
+    else k_offsets<false><<<blocks, kThreads, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+size_t scatter_smem(int max_digit_bits) { return scatter_smem_bytes(1 << max_digit_bits); }
+
+cudaError_t launch_scatter(const Ctx &c, int blocks, bool final_pass, int max_digit_bits, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    const size_t smem = scatter_smem_bytes(1 << max_digit_bits);
+    if (final_pass) k_scatter<true><<<blocks, kThreads, smem, st>>>(c);
+    else k_scatter<false><<<blocks, kThreads, smem, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_count<<<blocks, kThreads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1431,9 +1466,10 @@ cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32
 }
 
 cudaError_t configure_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_sort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    const int big = (int)scatter_smem_bytes(kMaxDigits);
+    cudaError_t e = cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_sort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+    e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
 }
@@ -1444,9 +1480,9 @@ int occupancy_spmm(bool smem_acc) {
     return n > 0 ? n : 1;
 }
 
-int occupancy_sort() {
+int occupancy_scatter(int digit_bits) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sort<true>, kThreads, kSortSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scatter<true>, kThreads, scatter_smem_bytes(1 << digit_bits));
     return n > 0 ? n : 1;
 }
 
