@@ -166,6 +166,37 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
                    const int32_t *labels, int32_t K, const gee_opts *opts, float *Z,
                    void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *status);
 
+/*
+ * gee_embed_static -- gee_embed without a workspace argument, for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is an interface addition.
+ *
+ * Who needs it: code that is handed device pointers by another framework but has no
+ * access to that framework's allocator, and latency-critical loops that must not call
+ * cudaMalloc (it can synchronise the whole device).  Instead of a caller workspace the
+ * call uses one scratch array of GEE_STATIC_WORKSPACE_BYTES (64 MiB) built into the
+ * library; every GPU that loads the library holds that memory until the process exits.
+ *
+ *   Arguments   as gee_embed, minus d_workspace / workspace_bytes; the caller still owns
+ *               and passes the inputs, d_Z and d_status.
+ *   Limit       returns GEE_ERR_TOO_LARGE, launching nothing, when
+ *               gee_workspace_size(E, N, K, d_w != NULL, opts) exceeds
+ *               GEE_STATIC_WORKSPACE_BYTES (about 4 million weighted directed edges on a
+ *               graph with more than 2048 nodes, about 6.6 million with at most 2048,
+ *               about twice that unweighted), and beyond gee_embed's own limits.
+ *   Allocation  none: no cudaMalloc, cudaFree or allocating library call.
+ *   Set-up      the first call on each device looks up the array's device address
+ *               (cudaGetSymbolAddress) with that device current; make that first call
+ *               before any stream capture.
+ *   Sharing     all calls on a device use the same array, which keeps the last call's
+ *               contents; each call clears what must start at zero itself.  Calls that
+ *               overlap on the GPU (different streams, different host threads) race on
+ *               the array and give wrong results: serialise them.
+ */
+#define GEE_STATIC_WORKSPACE_BYTES (64u << 20)
+int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                     const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *stream,
+                     uint32_t *d_status);
+
 /* Human-readable text of a gee_error code. */
 const char *gee_strerror(int code);
 

@@ -12,6 +12,7 @@ from ._native import (  # noqa: F401
     gee_class_counts,
     gee_embed,
     gee_embed_host,
+    gee_embed_static,
     gee_embed_timed,
     gee_host_workspace_size,
     gee_opts,

@@ -28,6 +28,7 @@ _SIGNATURES = {
     "gee_build_csr": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
                       ctypes.c_int),
     "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
+    "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "gee_embed_host": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
 }
 
@@ -139,3 +140,7 @@ def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_b
     return lib().gee_embed_host(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
                                 ptr(workspace), workspace_bytes, stream_handle(stream), ptr(status))
 
+
+def gee_embed_static(src, dst, w, E, N, labels, K, opts, Z, stream=None, d_status=None) -> int:
+    return lib().gee_embed_static(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
+                                  stream_handle(stream), ptr(d_status))

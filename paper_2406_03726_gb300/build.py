@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libgee.so")
-SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu"]
+SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu", "csrc/gee_static.cu"]
 HEADERS = ["csrc/gee_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
