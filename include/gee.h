@@ -121,10 +121,10 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
  *   range), 2 k_offsets (first pass), 3 k_scatter first pass (graphs with more than
  *   2^11 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final
  *   pass), 6 k_scatter final pass (writes the CSR), 7 k_rowscan (index_pointers,
- *   unweighted degrees), 8 k_hubprep (hub-row chunks), 9 k_wdeg (weighted degrees),
- *   10 k_spmm (Z with the fused epilogue).
+ *   unweighted degrees), 8 k_hubprep (hub-row chunks), 9 k_wdeg_hub and 10 k_wdeg_rows
+ *   (weighted degrees), 11 k_spmm_hub and 12 k_spmm_rows (Z with the fused epilogue).
  */
-#define GEE_NUM_PHASES 11
+#define GEE_NUM_PHASES 13
 int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                     const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
                     void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status,
@@ -196,6 +196,42 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
 int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                      const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *stream,
                      uint32_t *d_status);
+
+/* ------------------------------------------------------------------------------------
+ * Many graphs at once.  The graphs of a batch are embedded by the same kernels in one
+ * launch sequence (each kernel's work items span all graphs); each graph's Z is
+ * bit-identical to what gee_embed gives for it alone.  All graphs share one option set.
+ */
+typedef struct gee_graph {
+    const int32_t *src, *dst; /* device int32 [E] (NULL when E == 0) */
+    const float *w;           /* device float32 [E] or NULL (unweighted) */
+    const int32_t *labels;    /* device int32 [N] */
+    float *Z;                 /* device float32 [N][K] */
+    int64_t E;
+    int32_t N, K;
+} gee_graph;
+
+/* Workspace bytes for a batch (0 if a graph is invalid).  `graphs` is a HOST array. */
+size_t gee_batch_workspace_size(const gee_graph *graphs, int32_t G, const gee_opts *opts);
+
+/* Embed G graphs (HOST array of descriptors).  Copies the per-graph plan (about 300
+ * bytes per graph) into the workspace, then enqueues the kernels on `stream`.
+ * d_status: device uint32 [G] receiving each graph's GEE_STATUS_* bits, or NULL. */
+int gee_embed_batch(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                    size_t workspace_bytes, void *stream, uint32_t *d_status);
+
+/* A reusable batch plan: created once (plans, uploads the descriptors into the
+ * workspace and waits for the copy), then launched any number of times on the same
+ * inputs/outputs.  With use_graph != 0 the first launch captures the kernel sequence
+ * in a CUDA graph and later launches replay it.  The workspace must outlive the plan. */
+typedef struct gee_batch_plan gee_batch_plan;
+int gee_batch_plan_create(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                          size_t workspace_bytes, void *stream, gee_batch_plan **plan);
+int gee_batch_plan_launch(gee_batch_plan *plan, void *stream, uint32_t *d_status, int use_graph);
+/* The plan's launch sequence with CUDA events between phases (as gee_embed_timed): waits
+ * and stores the device time of each phase, in ms, into HOST phase_ms[GEE_NUM_PHASES]. */
+int gee_batch_plan_launch_timed(gee_batch_plan *plan, void *stream, float *phase_ms);
+void gee_batch_plan_destroy(gee_batch_plan *plan);
 
 /* Human-readable text of a gee_error code. */
 const char *gee_strerror(int code);

@@ -8,6 +8,14 @@ only allocate device memory with PyTorch and call it.
 from __future__ import annotations
 
 from ._native import (  # noqa: F401
+    gee_batch_plan_create,
+    gee_batch_plan_destroy,
+    gee_batch_plan_launch,
+    gee_batch_plan_launch_timed,
+    gee_batch_workspace_size,
+    gee_embed_batch,
+    gee_graph,
+    make_graphs,
     gee_build_csr,
     gee_class_counts,
     gee_embed,
@@ -34,7 +42,7 @@ STATUS_WEIGHT = 4
 STATUS_TIMEOUT = 8
 
 PHASES = ("memset", "k_prep", "k_offsets_first", "k_scatter_first", "k_count", "k_offsets_final",
-          "k_scatter_final", "k_rowscan", "k_hubprep", "k_wdeg", "k_spmm")
+          "k_scatter_final", "k_rowscan", "k_hubprep", "k_wdeg_hub", "k_wdeg_rows", "k_spmm_hub", "k_spmm_rows")
 
 MAX_N = 1 << 21
 MAX_E = 1 << 30
@@ -100,3 +108,48 @@ def class_counts(rowptr, col, N, labels, K, stream=None):
     C = torch.empty((N, K), dtype=torch.int32, device=labels.device)
     _check(gee_class_counts(rowptr, col, N, labels, K, C, stream), "gee_class_counts")
     return C
+
+
+class BatchPlan:
+    """A reusable plan for many graphs (device tensors), launched as one kernel sequence
+    (replayed as a CUDA graph with use_graph=True)."""
+
+    def __init__(self, graphs, flags=0, hub_threshold=0, lanes_per_row=0, device=None, stream=None):
+        import torch
+        self.opts = make_opts(flags, hub_threshold, lanes_per_row)
+        self.items = []
+        self.Z = []
+        for (src, dst, w, labels, N, K) in graphs:
+            Z = torch.empty((N, K), dtype=torch.float32, device=labels.device)
+            self.Z.append(Z)
+            self.items.append((src, dst, w, labels, Z, int(src.numel()), N, K))
+        self.G = len(self.items)
+        self.arr = make_graphs(self.items)
+        n = gee_batch_workspace_size(self.arr, self.G, self.opts)
+        if n == 0:
+            raise GeeError(1, "gee_batch_workspace_size")
+        self.ws = torch.empty(n, dtype=torch.uint8, device=device or graphs[0][3].device)
+        self.status = torch.zeros(self.G, dtype=torch.int32, device=self.ws.device)
+        rc, self.handle = gee_batch_plan_create(self.arr, self.G, self.opts, self.ws, n, stream)
+        _check(rc, "gee_batch_plan_create")
+
+    def launch(self, stream=None, use_graph=True, status=True):
+        rc = gee_batch_plan_launch(self.handle, stream, self.status if status else None, use_graph)
+        _check(rc, "gee_batch_plan_launch")
+        return self.Z
+
+    def launch_timed(self, phase_ms, stream=None):
+        """Launch with per-phase CUDA-event times written into the float32 array phase_ms."""
+        _check(gee_batch_plan_launch_timed(self.handle, stream, phase_ms), "gee_batch_plan_launch_timed")
+        return self.Z
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gee_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

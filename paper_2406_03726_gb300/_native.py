@@ -18,6 +18,12 @@ class gee_opts(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class gee_graph(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("E", ctypes.c_int64),
+                ("N", ctypes.c_int32), ("K", ctypes.c_int32)]
+
+
 _SIGNATURES = {
     "gee_version": ([], ctypes.c_int),
     "gee_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -29,6 +35,12 @@ _SIGNATURES = {
                       ctypes.c_int),
     "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
     "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "gee_batch_workspace_size": ([_P, _I32, _P], _SZ),
+    "gee_embed_batch": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
+    "gee_batch_plan_create": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
+    "gee_batch_plan_launch": ([_P, _P, _P, ctypes.c_int], ctypes.c_int),
+    "gee_batch_plan_launch_timed": ([_P, _P, _P], ctypes.c_int),
+    "gee_batch_plan_destroy": ([_P], None),
     "gee_embed_host": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
 }
 
@@ -144,3 +156,40 @@ def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_b
 def gee_embed_static(src, dst, w, E, N, labels, K, opts, Z, stream=None, d_status=None) -> int:
     return lib().gee_embed_static(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
                                   stream_handle(stream), ptr(d_status))
+
+
+def make_graphs(items):
+    """ctypes array of gee_graph from (src, dst, w, labels, Z, E, N, K) tuples."""
+    arr = (gee_graph * len(items))()
+    for i, (src, dst, w, labels, Z, E, N, K) in enumerate(items):
+        arr[i] = gee_graph(ptr(src), ptr(dst), ptr(w), ptr(labels), ptr(Z), E, N, K)
+    return arr
+
+
+def gee_batch_workspace_size(graphs, G, opts=None) -> int:
+    return lib().gee_batch_workspace_size(graphs, G, _opts_ref(opts))
+
+
+def gee_embed_batch(graphs, G, opts, workspace, workspace_bytes, stream=None, d_status=None) -> int:
+    return lib().gee_embed_batch(graphs, G, _opts_ref(opts), ptr(workspace), workspace_bytes,
+                                 stream_handle(stream), ptr(d_status))
+
+
+def gee_batch_plan_create(graphs, G, opts, workspace, workspace_bytes, stream=None):
+    """(return code, plan handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().gee_batch_plan_create(graphs, G, _opts_ref(opts), ptr(workspace), workspace_bytes,
+                                     stream_handle(stream), ctypes.byref(h))
+    return rc, h
+
+
+def gee_batch_plan_launch(plan, stream=None, d_status=None, use_graph=True) -> int:
+    return lib().gee_batch_plan_launch(plan, stream_handle(stream), ptr(d_status), 1 if use_graph else 0)
+
+
+def gee_batch_plan_destroy(plan) -> None:
+    lib().gee_batch_plan_destroy(plan)
+
+
+def gee_batch_plan_launch_timed(plan, stream=None, phase_ms=None) -> int:
+    return lib().gee_batch_plan_launch_timed(plan, stream_handle(stream), ptr(phase_ms))

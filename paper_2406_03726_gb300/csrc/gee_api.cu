@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 namespace gee {
 
@@ -24,14 +25,17 @@ size_t scatter_smem(int max_digit_bits);
 cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st);
-cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st);
-cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
+cudaError_t launch_wdeg(const Ctx &c, int hub_blocks, int row_blocks, cudaStream_t st);
+cudaError_t launch_spmm_hub(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
+cudaError_t launch_spmm_rows(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
 cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32_t N, const int32_t *y, int32_t K,
                                 int32_t *C, int blocks, cudaStream_t st);
 cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st);
 cudaError_t configure_kernels();
-int occupancy_spmm(bool smem_acc);
-int occupancy_wdeg();
+int occupancy_spmm_rows(bool smem_acc);
+int occupancy_spmm_hub(bool smem_acc);
+int occupancy_wdeg_rows();
+int occupancy_wdeg_hub();
 
 namespace {
 
@@ -42,8 +46,9 @@ constexpr size_t kSmemPerSM = 228 * 1024;   // shared memory per SM usable by CT
 struct DeviceInfo {
     bool ready = false;
     int sms = 0;
-    int occ_spmm[2] = {1, 1};
-    int occ_wdeg = 1;
+    int occ_rows[2] = {1, 1};  // k_spmm_rows without / with shared-memory accumulators
+    int occ_hub[2] = {1, 1};   // k_spmm_hub
+    int occ_wrows = 1, occ_whub = 1;
 };
 
 std::mutex g_mu;
@@ -57,9 +62,12 @@ int device_info(DeviceInfo &out) {
     if (!d.ready) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEE_ERR_CUDA;
         if (configure_kernels() != cudaSuccess) return GEE_ERR_CUDA;
-        d.occ_spmm[0] = occupancy_spmm(false);
-        d.occ_spmm[1] = occupancy_spmm(true);
-        d.occ_wdeg = occupancy_wdeg();
+        for (int i = 0; i < 2; ++i) {
+            d.occ_rows[i] = occupancy_spmm_rows(i == 1);
+            d.occ_hub[i] = occupancy_spmm_hub(i == 1);
+        }
+        d.occ_wrows = occupancy_wdeg_rows();
+        d.occ_whub = occupancy_wdeg_hub();
         d.ready = true;
     }
     out = d;
@@ -124,10 +132,11 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     }
     lpr = std::min(32, std::max(1, lpr));
     d.lpr_log2 = ilog2_pow2(lpr);
-    d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : 4096;
+    // rows longer than hub_C are split across CTAs: 64 vector loads per lane of the group
+    d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
     d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
-    d.rows_per_item = kWarps * (32 >> d.lpr_log2);
+    d.rows_per_item = 4 * (32 >> d.lpr_log2);  // four rounds of a warp's row groups
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
     // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
     // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
@@ -141,9 +150,8 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
 uint32_t hub_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / ((int64_t)d.hub_C + 1)); }
 uint32_t chunk_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / d.hub_C) + hub_cap_of(d) + 1; }
 
-// zero-initialised arrays of one graph
+// zero-initialised arrays of one graph (its status word is allocated by the caller)
 void layout_zero(Bump &b, GraphDesc &d) {
-    d.status = b.take<uint32_t>(1);
     d.rowcnt = b.take<int32_t>((size_t)d.N);
     d.nk = b.take<int32_t>((size_t)d.K);
     d.hist1 = b.take<uint32_t>((size_t)1 << first_bits(d));
@@ -190,37 +198,58 @@ gee_opts opts_or_default(const gee_opts *o) {
     return r;
 }
 
-// Full single-graph plan over a workspace base (nullptr = sizing only).
-struct SinglePlan {
-    GraphDesc d;
-    CallBufs cb;
-    size_t zero_bytes = 0;
-    size_t total_bytes = 0;
-};
-
-void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p) {
-    std::memset(&p.d, 0, sizeof(p.d));
-    std::memset(&p.cb, 0, sizeof(p.cb));
-    plan_params(s, o, want_deg, p.d);
-    p.cb.hub_cap = hub_cap_of(p.d);
-    p.cb.chunk_cap = chunk_cap_of(p.d);
-    p.cb.kmax = s.K;
-    Bump b{base};
-    layout_call_zero(b, p.cb);
-    layout_zero(b, p.d);
-    p.zero_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
-    layout_rest(b, p.d, s.weighted);
-    layout_call_rest(b, p.cb);
-    p.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+int check_opts(const gee_opts &o) {
+    if (o.reserved != 0 || o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
+        (o.lanes_per_row & (o.lanes_per_row - 1)))
+        return GEE_ERR_ARG;
+    return GEE_OK;
 }
 
 int cuda_check(cudaError_t e) { return e == cudaSuccess ? GEE_OK : GEE_ERR_CUDA; }
 
-#define GEE_TRY(x)                 \
-    do {                           \
-        int _rc = (x);             \
+#define GEE_TRY(x)                     \
+    do {                               \
+        int _rc = (x);                 \
         if (_rc != GEE_OK) return _rc; \
     } while (0)
+
+// ---- launch plan: everything the launch sequence needs, for one graph or many -----------
+
+struct LaunchPlan {
+    Ctx base;                        // g0 (one graph) or graphs (G > 1), and the call buffers
+    const int32_t *prefix[kNumPfx];  // device item prefixes per kernel (G > 1)
+    int32_t items[kNumPfx];          // total items per kernel
+    int b1max = 1, fmax = 1;         // widest digits (shared-memory size of k_scatter)
+    bool any_two = false, any_wdeg = false, smem_acc = false;
+    void *zero_base = nullptr;
+    size_t zero_bytes = 0;
+};
+
+void plan_items(const GraphDesc &d, int32_t it[kNumPfx]) {
+    const int node_tiles = (int)(((int64_t)d.N + kPrepTile - 1) / kPrepTile);
+    const bool two = d.npass == 2, edges = d.ranges > 0;
+    const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
+    it[kPfxPrep] = d.ranges + node_tiles;
+    it[kPfxOffs1] = edges ? ((1 << first_bits(d)) + 31) / 32 : 0;
+    it[kPfxScat1] = (edges && two) ? d.ranges : 0;
+    it[kPfxCount] = (edges && two) ? d.ranges : 0;
+    it[kPfxOffs2] = (edges && two) ? ((1 << d.fbits) + 31) / 32 : 0;
+    it[kPfxScatF] = d.ranges;
+    it[kPfxScan] = d.tiles_n;
+    it[kPfxRows] = row_items;
+    it[kPfxWRows] = d.wdeg ? row_items : 0;
+}
+
+void plan_accumulate(LaunchPlan &lp, const GraphDesc &d) {
+    int32_t it[kNumPfx];
+    plan_items(d, it);
+    for (int k = 0; k < kNumPfx; ++k) lp.items[k] += it[k];
+    lp.b1max = std::max(lp.b1max, d.npass == 2 ? d.lbits : 1);
+    lp.fmax = std::max(lp.fmax, d.fbits);
+    lp.any_two = lp.any_two || d.npass == 2;
+    lp.any_wdeg = lp.any_wdeg || d.wdeg;
+    lp.smem_acc = lp.smem_acc || d.K > kRegK;
+}
 
 // Phases of one call, in launch order (the GEE_NUM_PHASES list in gee.h).
 enum Phase {
@@ -233,7 +262,9 @@ enum Phase {
     kPhScatF,
     kPhRowscan,
     kPhHubprep,
+    kPhWdegHub,
     kPhWdeg,
+    kPhSpmmHub,
     kPhSpmm,
     kNumPhases
 };
@@ -259,46 +290,86 @@ inline int mark(PhaseEvents *pe, int ph, cudaStream_t st) {
         }                                            \
     } while (0)
 
-// Enqueue the path for one planned graph: the CSR build, degrees and node table, and
-// (embed) the product with its epilogue.
-int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe, bool embed) {
-    const GraphDesc &d = p.d;
-    Ctx c;
-    std::memset(&c, 0, sizeof(c));
-    c.g0 = d;
-    c.G = 1;
-    c.cb = p.cb;
+// Enqueue the path: the CSR build, degrees and node table, and (embed) the product with
+// its epilogue.  One kernel launch per phase covers every graph of the plan.
+int run_plan(const LaunchPlan &lp, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe, bool embed) {
     if (pe) std::memset(pe->ran, 0, sizeof(pe->ran));
-    const bool two = d.npass == 2;
-    const int node_tiles = (int)(((int64_t)d.N + kPrepTile - 1) / kPrepTile);
-    const int blk1 = ((1 << first_bits(d)) + 31) / 32, blk2 = ((1 << d.fbits) + 31) / 32;
-    const bool edges = d.ranges > 0;
-    GEE_PHASE(kPhMemset, true, cudaMemsetAsync(p.cb.cs, 0, p.zero_bytes, st));
-    c.items = d.ranges + node_tiles;
-    GEE_PHASE(kPhPrep, c.items > 0, launch_prep(c, c.items, st));
-    c.items = blk1;
-    GEE_PHASE(kPhOffs1, edges, launch_offsets(c, blk1, false, st));
-    c.items = d.ranges;
-    GEE_PHASE(kPhScat1, edges && two, launch_scatter(c, d.ranges, false, d.lbits, st));
-    GEE_PHASE(kPhCount, edges && two, launch_count(c, d.ranges, st));
-    c.items = blk2;
-    GEE_PHASE(kPhOffs2, edges && two, launch_offsets(c, blk2, true, st));
-    c.items = d.ranges;
-    GEE_PHASE(kPhScatF, edges, launch_scatter(c, d.ranges, true, d.fbits, st));
-    c.items = d.tiles_n;
-    GEE_PHASE(kPhRowscan, d.tiles_n > 0, launch_rowscan(c, d.tiles_n, st));
-    const bool hubs = p.cb.hub_cap > 0 && (embed || d.wdeg);
-    GEE_PHASE(kPhHubprep, hubs, launch_hubprep(p.cb, st));
-    const int row_items = (int)(((int64_t)d.N + d.rows_per_item - 1) / d.rows_per_item);
-    c.items = row_items;
-    const int64_t max_items = (int64_t)row_items + (p.cb.hub_cap > 0 ? p.cb.chunk_cap : 0);
-    const int wgrid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_wdeg);
-    GEE_PHASE(kPhWdeg, d.wdeg && wgrid > 0, launch_wdeg(c, wgrid, st));
-    const bool smem = d.K > kRegK;
-    const int sgrid = (int)std::min<int64_t>(max_items, (int64_t)dev.sms * dev.occ_spmm[smem ? 1 : 0]);
-    GEE_PHASE(kPhSpmm, embed && sgrid > 0, launch_spmm(c, sgrid, smem, st));
+    Ctx c = lp.base;
+    auto ctx = [&](int kind) {
+        c.prefix = lp.prefix[kind];
+        c.items = lp.items[kind];
+        return c;
+    };
+    const CallBufs &cb = lp.base.cb;
+    GEE_PHASE(kPhMemset, lp.zero_bytes > 0, cudaMemsetAsync(lp.zero_base, 0, lp.zero_bytes, st));
+    GEE_PHASE(kPhPrep, lp.items[kPfxPrep] > 0, launch_prep(ctx(kPfxPrep), lp.items[kPfxPrep], st));
+    GEE_PHASE(kPhOffs1, lp.items[kPfxOffs1] > 0, launch_offsets(ctx(kPfxOffs1), lp.items[kPfxOffs1], false, st));
+    GEE_PHASE(kPhScat1, lp.items[kPfxScat1] > 0,
+              launch_scatter(ctx(kPfxScat1), lp.items[kPfxScat1], false, lp.b1max, st));
+    GEE_PHASE(kPhCount, lp.items[kPfxCount] > 0, launch_count(ctx(kPfxCount), lp.items[kPfxCount], st));
+    GEE_PHASE(kPhOffs2, lp.items[kPfxOffs2] > 0, launch_offsets(ctx(kPfxOffs2), lp.items[kPfxOffs2], true, st));
+    GEE_PHASE(kPhScatF, lp.items[kPfxScatF] > 0, launch_scatter(ctx(kPfxScatF), lp.items[kPfxScatF], true, lp.fmax, st));
+    GEE_PHASE(kPhRowscan, lp.items[kPfxScan] > 0, launch_rowscan(ctx(kPfxScan), lp.items[kPfxScan], st));
+    const bool hubs = cb.hub_cap > 0 && (embed || lp.any_wdeg);
+    GEE_PHASE(kPhHubprep, hubs, launch_hubprep(cb, st));
+    const int64_t hub_grid_max = cb.hub_cap > 0 ? cb.chunk_cap : 0;
+    const int whub = (int)std::min<int64_t>(lp.any_wdeg ? hub_grid_max : 0, (int64_t)dev.sms * dev.occ_whub);
+    const int64_t wrow_items = lp.items[kPfxWRows];
+    const int wrows = (int)std::min<int64_t>((wrow_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_wrows);
+    GEE_PHASE(kPhWdegHub, whub > 0, launch_wdeg(ctx(kPfxWRows), whub, 0, st));
+    GEE_PHASE(kPhWdeg, wrows > 0, launch_wdeg(ctx(kPfxWRows), 0, wrows, st));
+    const int sm = lp.smem_acc ? 1 : 0;
+    const int shub = (int)std::min<int64_t>(hub_grid_max, (int64_t)dev.sms * dev.occ_hub[sm]);
+    const int64_t row_items = lp.items[kPfxRows];
+    const int srows = (int)std::min<int64_t>((row_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_rows[sm]);
+    GEE_PHASE(kPhSpmmHub, embed && shub > 0, launch_spmm_hub(ctx(kPfxRows), shub, lp.smem_acc, st));
+    GEE_PHASE(kPhSpmm, embed && srows > 0, launch_spmm_rows(ctx(kPfxRows), srows, lp.smem_acc, st));
     GEE_TRY(mark(pe, kNumPhases, st));
     return GEE_OK;
+}
+
+// ---- one graph ------------------------------------------------------------------------
+
+struct SinglePlan {
+    GraphDesc d;
+    CallBufs cb;
+    size_t zero_bytes = 0;
+    size_t total_bytes = 0;
+};
+
+void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p) {
+    std::memset(&p.d, 0, sizeof(p.d));
+    std::memset(&p.cb, 0, sizeof(p.cb));
+    plan_params(s, o, want_deg, p.d);
+    p.cb.hub_cap = hub_cap_of(p.d);
+    p.cb.chunk_cap = chunk_cap_of(p.d);
+    p.cb.kmax = s.K;
+    Bump b{base};
+    layout_call_zero(b, p.cb);
+    p.d.status = b.take<uint32_t>(1);
+    layout_zero(b, p.d);
+    p.zero_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+    layout_rest(b, p.d, s.weighted);
+    layout_call_rest(b, p.cb);
+    p.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+}
+
+LaunchPlan launch_plan_single(const SinglePlan &p) {
+    LaunchPlan lp;
+    std::memset(&lp.base, 0, sizeof(lp.base));
+    std::memset(lp.prefix, 0, sizeof(lp.prefix));
+    std::memset(lp.items, 0, sizeof(lp.items));
+    lp.base.g0 = p.d;
+    lp.base.G = 1;
+    lp.base.cb = p.cb;
+    plan_accumulate(lp, p.d);
+    lp.zero_base = p.cb.cs;
+    lp.zero_bytes = p.zero_bytes;
+    return lp;
+}
+
+int run_single(const SinglePlan &p, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe, bool embed) {
+    return run_plan(launch_plan_single(p), dev, st, pe, embed);
 }
 
 int check_ws(void *ws, size_t bytes, size_t need) {
@@ -352,9 +423,7 @@ int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int
     GEE_TRY(check_inputs(d_src, d_dst, E, N, d_labels));
     if (N > 0 && !d_Z) return GEE_ERR_ARG;
     const gee_opts o = opts_or_default(opts);
-    if (o.reserved != 0 || o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
-        (o.lanes_per_row & (o.lanes_per_row - 1)))
-        return GEE_ERR_ARG;
+    GEE_TRY(check_opts(o));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (N == 0) {
         if (pe) {
@@ -528,6 +597,245 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
     GEE_TRY(cuda_check(cudaStreamSynchronize(st)));
     if (status) *status = h_status;
     return h_status ? GEE_ERR_DATA : GEE_OK;
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// Many graphs in one launch sequence
+
+struct gee_batch_plan {
+    int32_t G = 0;
+    std::vector<unsigned char> staging;  // host copy of the descriptors and item prefixes
+    void *d_meta = nullptr;              // their place in the workspace
+    gee::LaunchPlan lp;
+    uint32_t *d_statuses = nullptr;      // [G] status words, contiguous
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace gee {
+namespace {
+
+constexpr int32_t kBatchRangeTiles = 8;  // 16K-edge ranges: many ranges, one CTA each
+
+struct BatchLayout {
+    std::vector<GraphDesc> descs;
+    std::vector<int32_t> prefix;  // [kNumPfx][G + 1]
+    LaunchPlan lp;
+    uint32_t *statuses = nullptr;
+    GraphDesc *d_descs = nullptr;
+    int32_t *d_prefix = nullptr;
+    size_t meta_bytes = 0;
+    size_t total_bytes = 0;
+};
+
+int check_graph(const gee_graph &g) {
+    GEE_TRY(check_shape(g.E, g.N, g.K));
+    GEE_TRY(check_inputs(g.src, g.dst, g.E, g.N, g.labels));
+    if (g.N > 0 && !g.Z) return GEE_ERR_ARG;
+    return GEE_OK;
+}
+
+int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base, BatchLayout &L) {
+    if (G < 1 || !graphs) return GEE_ERR_ARG;
+    GEE_TRY(check_opts(o));
+    L.descs.assign((size_t)G, GraphDesc{});
+    CallBufs cb;
+    std::memset(&cb, 0, sizeof(cb));
+    cb.kmax = 1;
+    uint64_t hub_cap = 0, chunk_cap = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        GEE_TRY(check_graph(graphs[g]));
+        GraphDesc &d = L.descs[g];
+        std::memset(&d, 0, sizeof(d));
+        plan_params(Shape{graphs[g].E, graphs[g].N, graphs[g].K, graphs[g].w != nullptr}, o, false, d);
+        d.range_tiles = kBatchRangeTiles;  // only changes how work is cut, never the result
+        d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
+        hub_cap += hub_cap_of(d);
+        chunk_cap += chunk_cap_of(d);
+        cb.kmax = std::max(cb.kmax, d.K);
+    }
+    if (hub_cap >= 0xffffffffull || chunk_cap >= 0xffffffffull) return GEE_ERR_TOO_LARGE;
+    cb.hub_cap = (uint32_t)hub_cap;
+    cb.chunk_cap = (uint32_t)chunk_cap;
+    Bump b{base};
+    layout_call_zero(b, cb);
+    L.statuses = b.take<uint32_t>((size_t)G);
+    for (int32_t g = 0; g < G; ++g) {
+        layout_zero(b, L.descs[g]);
+        L.descs[g].status = L.statuses ? L.statuses + g : nullptr;
+    }
+    const size_t zero_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+    L.d_descs = b.take<GraphDesc>((size_t)G);
+    L.d_prefix = b.take<int32_t>((size_t)kNumPfx * (G + 1));
+    L.meta_bytes = (reinterpret_cast<size_t>(L.d_prefix) + sizeof(int32_t) * (size_t)kNumPfx * (G + 1)) -
+                   reinterpret_cast<size_t>(L.d_descs);
+    for (int32_t g = 0; g < G; ++g) layout_rest(b, L.descs[g], graphs[g].w != nullptr);
+    layout_call_rest(b, cb);
+    L.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+
+    LaunchPlan &lp = L.lp;
+    std::memset(&lp.base, 0, sizeof(lp.base));
+    std::memset(lp.items, 0, sizeof(lp.items));
+    lp.base.G = G;
+    lp.base.graphs = L.d_descs;
+    lp.base.cb = cb;
+    L.prefix.assign((size_t)kNumPfx * (G + 1), 0);
+    for (int32_t g = 0; g < G; ++g) {
+        GraphDesc &d = L.descs[g];
+        d.src = graphs[g].src;
+        d.dst = graphs[g].dst;
+        d.w = graphs[g].w;
+        d.y = graphs[g].labels;
+        d.Z = graphs[g].Z;
+        int32_t it[kNumPfx];
+        plan_items(d, it);
+        for (int k = 0; k < kNumPfx; ++k) {
+            const int64_t next = (int64_t)L.prefix[(size_t)k * (G + 1) + g] + it[k];
+            if (next >= INT32_MAX) return GEE_ERR_TOO_LARGE;
+            L.prefix[(size_t)k * (G + 1) + g + 1] = (int32_t)next;
+        }
+        plan_accumulate(lp, d);
+    }
+    for (int k = 0; k < kNumPfx; ++k) lp.prefix[k] = L.d_prefix ? L.d_prefix + (size_t)k * (G + 1) : nullptr;
+    lp.zero_base = cb.cs;
+    lp.zero_bytes = zero_bytes;
+    return GEE_OK;
+}
+
+// host image of [d_descs, d_prefix end) to copy into the workspace
+void batch_staging(const BatchLayout &L, std::vector<unsigned char> &out) {
+    out.assign(L.meta_bytes, 0);
+    std::memcpy(out.data(), L.descs.data(), sizeof(GraphDesc) * L.descs.size());
+    const size_t poff = reinterpret_cast<size_t>(L.d_prefix) - reinterpret_cast<size_t>(L.d_descs);
+    std::memcpy(out.data() + poff, L.prefix.data(), sizeof(int32_t) * L.prefix.size());
+}
+
+int batch_prepare(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_ws, size_t ws_bytes,
+                  BatchLayout &L) {
+    const gee_opts o = opts_or_default(opts);
+    GEE_TRY(plan_batch(graphs, G, o, nullptr, L));
+    GEE_TRY(check_ws(d_ws, ws_bytes, L.total_bytes));
+    return plan_batch(graphs, G, o, static_cast<char *>(d_ws), L);
+}
+
+}  // namespace
+}  // namespace gee
+
+extern "C" {
+
+size_t gee_batch_workspace_size(const gee_graph *graphs, int32_t G, const gee_opts *opts) {
+    gee::BatchLayout L;
+    if (gee::plan_batch(graphs, G, gee::opts_or_default(opts), nullptr, L) != GEE_OK) return 0;
+    return L.total_bytes;
+}
+
+int gee_embed_batch(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                    size_t workspace_bytes, void *stream, uint32_t *d_status) {
+    gee::BatchLayout L;
+    GEE_TRY(gee::batch_prepare(graphs, G, opts, d_workspace, workspace_bytes, L));
+    gee::DeviceInfo dev;
+    GEE_TRY(gee::device_info(dev));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<unsigned char> staging;
+    gee::batch_staging(L, staging);
+    GEE_TRY(gee::cuda_check(cudaMemcpyAsync(L.d_descs, staging.data(), staging.size(), cudaMemcpyHostToDevice, st)));
+    // the copy reads pageable host memory: it is staged before cudaMemcpyAsync returns
+    GEE_TRY(gee::run_plan(L.lp, dev, st, nullptr, true));
+    if (d_status)
+        GEE_TRY(gee::cuda_check(
+            cudaMemcpyAsync(d_status, L.statuses, sizeof(uint32_t) * (size_t)G, cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+
+int gee_batch_plan_create(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                          size_t workspace_bytes, void *stream, gee_batch_plan **out) {
+    if (!out) return GEE_ERR_ARG;
+    *out = nullptr;
+    gee::BatchLayout L;
+    GEE_TRY(gee::batch_prepare(graphs, G, opts, d_workspace, workspace_bytes, L));
+    gee::DeviceInfo dev;
+    GEE_TRY(gee::device_info(dev));
+    gee_batch_plan *p = new gee_batch_plan();
+    p->G = G;
+    p->lp = L.lp;
+    p->d_statuses = L.statuses;
+    p->d_meta = L.d_descs;
+    cudaGetDevice(&p->device);
+    gee::batch_staging(L, p->staging);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = gee::cuda_check(cudaMemcpyAsync(p->d_meta, p->staging.data(), p->staging.size(),
+                                             cudaMemcpyHostToDevice, st));
+    if (rc == GEE_OK) rc = gee::cuda_check(cudaStreamSynchronize(st));
+    if (rc != GEE_OK) {
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return GEE_OK;
+}
+
+int gee_batch_plan_launch(gee_batch_plan *p, void *stream, uint32_t *d_status, int use_graph) {
+    if (!p) return GEE_ERR_ARG;
+    gee::DeviceInfo dev;
+    GEE_TRY(gee::device_info(dev));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (use_graph) {
+        if (!p->exec) {
+            cudaStream_t cap = nullptr;
+            GEE_TRY(gee::cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)));
+            int rc = gee::cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            if (rc == GEE_OK) {
+                const int run_rc = gee::run_plan(p->lp, dev, cap, nullptr, true);
+                cudaGraph_t graph = nullptr;
+                const int end_rc = gee::cuda_check(cudaStreamEndCapture(cap, &graph));
+                rc = run_rc != GEE_OK ? run_rc : end_rc;
+                if (rc == GEE_OK) rc = gee::cuda_check(cudaGraphInstantiate(&p->exec, graph, 0));
+                if (rc == GEE_OK) p->graph = graph;
+                else if (graph) cudaGraphDestroy(graph);
+            }
+            cudaStreamDestroy(cap);
+            GEE_TRY(rc);
+        }
+        GEE_TRY(gee::cuda_check(cudaGraphLaunch(p->exec, st)));
+    } else {
+        GEE_TRY(gee::run_plan(p->lp, dev, st, nullptr, true));
+    }
+    if (d_status)
+        GEE_TRY(gee::cuda_check(cudaMemcpyAsync(d_status, p->d_statuses, sizeof(uint32_t) * (size_t)p->G,
+                                                cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+
+int gee_batch_plan_launch_timed(gee_batch_plan *p, void *stream, float *phase_ms) {
+    if (!p || !phase_ms) return GEE_ERR_ARG;
+    gee::DeviceInfo dev;
+    GEE_TRY(gee::device_info(dev));
+    gee::PhaseEvents pe;
+    for (int i = 0; i <= gee::kNumPhases; ++i)
+        if (cudaEventCreate(&pe.ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(pe.ev[j]);
+            return GEE_ERR_CUDA;
+        }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = gee::run_plan(p->lp, dev, st, &pe, true);
+    if (rc == GEE_OK && cudaEventSynchronize(pe.ev[gee::kNumPhases]) != cudaSuccess) rc = GEE_ERR_CUDA;
+    for (int i = 0; i < gee::kNumPhases; ++i) {
+        float ms = -1.0f;
+        if (rc == GEE_OK && pe.ran[i] && cudaEventElapsedTime(&ms, pe.ev[i], pe.ev[i + 1]) != cudaSuccess) ms = -1.0f;
+        phase_ms[i] = ms;
+    }
+    for (int i = 0; i <= gee::kNumPhases; ++i) cudaEventDestroy(pe.ev[i]);
+    return rc;
+}
+
+void gee_batch_plan_destroy(gee_batch_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
 }
 
 }  // extern "C"

@@ -907,33 +907,48 @@ __device__ __forceinline__ int find_hub(const uint32_t *off, int H, uint32_t ite
     return lo;
 }
 
-// Work-stealing loop shared by k_wdeg and k_spmm: items [0, hub_chunks) are hub chunks,
-// the next c.items are blocks of light rows.
-struct ItemRef {
-    int kind;   // 0 = hub chunk, 1 = light rows, -1 = done
-    int local;  // chunk index within hub / row block within graph
-    int hub;    // hub entry
-};
+// Work item claiming.  CTA-level (hub chunks, which need the whole CTA) and warp-level
+// (light rows: every warp claims and finishes its own rows, with no CTA barrier, so a
+// long row never holds up the other warps of its CTA).
+__device__ __forceinline__ int cta_claim(uint32_t *ctr, int *s_it) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_it = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    return *s_it;
+}
 
-__device__ __forceinline__ ItemRef next_item(const Ctx &c, int ctr, int *s_it, uint32_t hub_chunks, int H) {
-    __syncthreads();
-    if (threadIdx.x == 0) *s_it = (int)atomicAdd(&c.cb.cs->ctr[ctr], 1u);
-    __syncthreads();
-    const uint32_t it = (uint32_t)*s_it;
-    ItemRef r;
-    r.hub = -1;
-    if (it < hub_chunks) {
-        r.kind = 0;
-        r.hub = find_hub(c.cb.chunk_off, H, it);
-        r.local = (int)(it - __ldcg(c.cb.chunk_off + r.hub));
-    } else if (it - hub_chunks < (uint32_t)c.items) {
-        r.kind = 1;
-        r.local = (int)(it - hub_chunks);
-    } else {
-        r.kind = -1;
-        r.local = 0;
+__device__ __forceinline__ uint32_t warp_claim(uint32_t *ctr) {
+    uint32_t it = 0;
+    if ((threadIdx.x & 31) == 0) it = atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// Copy graph g's descriptor into this warp's shared slot.
+__device__ __forceinline__ void warp_load_desc(const Ctx &c, int g, GraphDesc *slot) {
+    const int lane = threadIdx.x & 31;
+    if (c.G > 1) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(c.graphs + g);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(slot);
+        for (int i = lane; i < (int)(sizeof(GraphDesc) / 4); i += 32) dst[i] = __ldg(src + i);
+    } else if (lane == 0) {
+        *slot = c.g0;
     }
-    return r;
+    __syncwarp();
+}
+
+// Resolve a light-row item to (graph, local block) for the whole warp.
+__device__ __forceinline__ int warp_item_graph(const Ctx &c, uint32_t it, int &local) {
+    int g = 0, base = 0;
+    if (c.G > 1) {
+        if ((threadIdx.x & 31) == 0) {
+            g = find_graph(c.prefix, c.G, (int)it);
+            base = __ldg(c.prefix + g);
+        }
+        g = __shfl_sync(0xffffffffu, g, 0);
+        base = __shfl_sync(0xffffffffu, base, 0);
+    }
+    local = (int)it - base;
+    return g;
 }
 
 // clamp a CSR row range to [0, E] (only matters after a reported failure)
@@ -945,7 +960,7 @@ __device__ __forceinline__ void row_range(const GraphDesc &g, int64_t row, int64
 }
 
 // ------------------------------------------------------------------------------------
-// k_wdeg: D_ii = sum_j e_ij (+1) for weighted graphs, then D^-1/2 and the node table
+// weighted degrees: D_ii = sum_j e_ij (+1), then D^-1/2 and the node table
 
 __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
     float t = s + v;
@@ -954,58 +969,78 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
     s = t;
 }
 
-__global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
+// hub rows: one CTA per chunk, FP64 partials, the last CTA of the row sums them in order
+__global__ void __launch_bounds__(kThreads) k_wdeg_hub(Ctx c) {
     __shared__ GraphDesc sg;
-    __shared__ int sl[2];
     __shared__ int s_it;
     __shared__ double s_red[kThreads];
     __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
     for (;;) {
-        ItemRef r = next_item(c, 3, &s_it, hub_chunks, H);
-        if (r.kind < 0) break;
-        if (r.kind == 0) {
-            const HubEntry he = c.cb.hubs[r.hub];
-            load_desc_idx(c, he.g, &sg);
-            if (!sg.wdeg) continue;  // degree and node table already written by k_rowscan
-            int64_t rs, re;
-            row_range(sg, he.row, rs, re);
-            const int64_t cs = rs + (int64_t)r.local * sg.hub_C;
-            const int64_t ce = min(re, cs + sg.hub_C);
-            float s = 0.f, cc = 0.f;
-            for (int64_t e = cs + tid; e < ce; e += kThreads) neumaier_add(s, cc, ld_stream(sg.val + e));
-            s_red[tid] = (double)s + (double)cc;  // FP64 for the heavy-row reduction
+        const int it = cta_claim(&c.cb.cs->ctr[3], &s_it);
+        if ((uint32_t)it >= hub_chunks) break;
+        const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
+        const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
+        const HubEntry he = c.cb.hubs[hub];
+        load_desc_idx(c, he.g, &sg);
+        if (!sg.wdeg) continue;  // degree and node table already written by k_rowscan
+        int64_t rs, re;
+        row_range(sg, he.row, rs, re);
+        const int64_t cs = rs + (int64_t)chunk * sg.hub_C;
+        const int64_t ce = min(re, cs + sg.hub_C);
+        float s = 0.f, cc = 0.f;
+        for (int64_t e = cs + tid; e < ce; e += kThreads) neumaier_add(s, cc, ld_stream(sg.val + e));
+        s_red[tid] = (double)s + (double)cc;  // FP64 for the heavy-row reduction
+        __syncthreads();
+        for (int o = kThreads / 2; o > 0; o >>= 1) {
+            if (tid < o) s_red[tid] += s_red[tid + o];
             __syncthreads();
-            for (int o = kThreads / 2; o > 0; o >>= 1) {
-                if (tid < o) s_red[tid] += s_red[tid + o];
-                __syncthreads();
-            }
-            if (tid == 0) {
-                const uint32_t slot = __ldcg(c.cb.chunk_off + r.hub) + (uint32_t)r.local;
-                if (slot < c.cb.chunk_cap) c.cb.part_deg[slot] = s_red[0];
-                __threadfence();
-                const uint32_t arrived = atomicAdd(c.cb.arrive_deg + r.hub, 1u);
-                s_last = (arrived == (uint32_t)he.nch - 1u);
-            }
-            __syncthreads();
-            if (s_last && tid == 0) {
-                __threadfence();
-                const uint32_t off = __ldcg(c.cb.chunk_off + r.hub);
-                double tot = 0.0;
-                for (int k = 0; k < he.nch; ++k)
-                    if (off + k < c.cb.chunk_cap) tot += __ldcg(c.cb.part_deg + off + k);
-                const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
-                write_node(sg, he.row, (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
-            }
-        } else {
-            const int t = load_desc(c, r.local, &sg, sl, c.prefix);
-            if (!sg.wdeg) continue;
-            const int lpr = 1 << sg.lpr_log2;
-            const int gpw = 32 >> sg.lpr_log2;         // row groups per warp
-            const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
-            const int64_t row = (int64_t)t * sg.rows_per_item + warp * gpw + grp;
+        }
+        if (tid == 0) {
+            const uint32_t slot = __ldcg(c.cb.chunk_off + hub) + (uint32_t)chunk;
+            if (slot < c.cb.chunk_cap) c.cb.part_deg[slot] = s_red[0];
+            __threadfence();
+            const uint32_t arrived = atomicAdd(c.cb.arrive_deg + hub, 1u);
+            s_last = (arrived == (uint32_t)he.nch - 1u);
+        }
+        __syncthreads();
+        if (s_last && tid == 0) {
+            __threadfence();
+            const uint32_t off = __ldcg(c.cb.chunk_off + hub);
+            double tot = 0.0;
+            for (int k = 0; k < he.nch; ++k)
+                if (off + k < c.cb.chunk_cap) tot += __ldcg(c.cb.part_deg + off + k);
+            const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
+            write_node(sg, he.row, (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
+        }
+    }
+}
+
+// light rows: a group of lanes per row, 16-byte loads, Neumaier-compensated FP32 per
+// lane, deterministic two-sum tree over the group
+__global__ void __launch_bounds__(kThreads) k_wdeg_rows(Ctx c) {
+    __shared__ GraphDesc wd[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cur = -1;
+    for (;;) {
+        const uint32_t it = warp_claim(&c.cb.cs->ctr[6]);
+        if (it >= (uint32_t)c.items) break;
+        int blk;
+        const int g = warp_item_graph(c, it, blk);
+        if (g != cur) {
+            __syncwarp();
+            warp_load_desc(c, g, &wd[warp]);
+            cur = g;
+        }
+        const GraphDesc &sg = wd[warp];
+        if (!sg.wdeg) continue;
+        const int lpr = 1 << sg.lpr_log2;
+        const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
+        const int rows_per_round = 32 >> sg.lpr_log2;
+        for (int r0 = 0; r0 < sg.rows_per_item; r0 += rows_per_round) {
+            const int64_t row = (int64_t)blk * sg.rows_per_item + r0 + grp;
             float s = 0.f, cc = 0.f;
             bool active = false;
             if (row < sg.N) {
@@ -1013,17 +1048,23 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
                 row_range(sg, row, rs, re);
                 if (re - rs <= sg.hub_C) {
                     active = true;
-                    for (int64_t e = rs + gl; e < re; e += lpr) neumaier_add(s, cc, ld_stream(sg.val + e));
+                    const int64_t a0 = rs & ~(int64_t)3;
+                    for (int64_t b = a0 + 4 * gl; b < re; b += 4 * lpr) {
+                        const float4 v = ld_stream4(sg.val + b);
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (b + q >= rs && b + q < re) neumaier_add(s, cc, vv[q]);
+                    }
                 }
             }
-            // deterministic tree over the group, result broadcast from the group's lane 0
+            // deterministic tree over the group; the result is taken from its lane 0
             for (int o = lpr >> 1; o > 0; o >>= 1) {
                 const float s2 = __shfl_down_sync(0xffffffffu, s, o);
                 const float c2 = __shfl_down_sync(0xffffffffu, cc, o);
                 if (gl < o) {
                     float e;
-                    const float t2 = two_sum(s, s2, e);
-                    s = t2;
+                    s = two_sum(s, s2, e);
                     cc = cc + (c2 + e);
                 }
             }
@@ -1036,7 +1077,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
 }
 
 // ------------------------------------------------------------------------------------
-// k_spmm: label-gather product + fused epilogue
+// label-gather product + fused epilogue
 
 // Accumulate val_ij * s_j into per-lane accumulators for the entries [lo, hi) of a row,
 // this lane being lane `gl` of a group of `gsz` lanes.  Vector loads of 4 entries from
@@ -1076,9 +1117,10 @@ __device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t 
     }
 }
 
-// Same, into a per-warp shared-memory accumulator sacc[k * 32 + lane] (K up to 64).
+// Same, into a per-warp shared-memory accumulator sacc[k * 32 + lane] (K up to 64),
+// recording the touched classes in a 64-bit mask (tlo: classes 0-31, thi: 32-63).
 __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
-                                         float *sacc, int lane, uint32_t &err) {
+                                         float *sacc, int lane, uint32_t &tlo, uint32_t &thi, uint32_t &err) {
     const int64_t a0 = lo & ~(int64_t)3;
     const bool has_w = g.val != nullptr && g.w != nullptr;
     const uint32_t N = (uint32_t)g.N;
@@ -1104,13 +1146,15 @@ __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t
                 if (j >= N) { err |= kStTimeout; continue; }
                 const int2 t = __ldg(g.tab + j);
                 sacc[t.x * 32 + lane] += vv[q] * __int_as_float(t.y);
+                if (t.x < 32) tlo |= 1u << t.x;
+                else thi |= 1u << (t.x - 32);
             }
         }
     }
 }
 
-// Epilogue for one row given its class totals: augmentation term, D_ii^-1/2, row 2-norm.
-// `get(k)` returns the total of class k (k < K); writes Z[row][k] for k = first, first+stride...
+// Epilogue of a row: augmentation term s_i on the row's own class, D_ii^-1/2 scaling
+// (Laplacian), then the 2-norm of the row (correlation).
 struct RowTail {
     float dv;     // D_ii^-1/2 (1 without the Laplacian)
     int yi;       // class of the row's node (0 if unlabelled; then si = 0)
@@ -1137,14 +1181,9 @@ __device__ __forceinline__ float finish_entry(float total, int k, const RowTail 
     return v;
 }
 
-constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
-
+// one light row per lane group, K <= 8: register accumulators, butterfly over the group
 template <int KR>
-__device__ __forceinline__ void light_rows_reg(const GraphDesc &g, int t, int lane, int warp, uint32_t &err) {
-    const int lpr = 1 << g.lpr_log2;
-    const int gpw = 32 >> g.lpr_log2;
-    const int grp = lane >> g.lpr_log2, gl = lane & (lpr - 1);
-    const int64_t row = (int64_t)t * g.rows_per_item + warp * gpw + grp;
+__device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, int gl, int lpr, uint32_t &err) {
     float acc[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
@@ -1184,39 +1223,52 @@ __device__ __forceinline__ void light_rows_reg(const GraphDesc &g, int t, int la
     }
 }
 
-__device__ __forceinline__ void light_rows_smem(const GraphDesc &g, int t, int lane, int warp, float *sacc,
-                                                uint32_t &err) {
-    const int lpr = 1 << g.lpr_log2;
-    const int gpw = 32 >> g.lpr_log2;
-    const int grp = lane >> g.lpr_log2, gl = lane & (lpr - 1);
-    const int64_t row = (int64_t)t * g.rows_per_item + warp * gpw + grp;
+// one light row per lane group, 8 < K <= 64: per-lane shared-memory columns.  The
+// accumulator is all-zero between rows; only the classes the row touched are reduced
+// (lane gl of the group owns the classes k = gl mod lpr, reads the group's columns in a
+// rotated order, which is free of bank conflicts) and cleared again.
+__device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, int gl, int lpr, float *sacc,
+                                               int lane, uint32_t &err) {
     const int K = g.K;
-    for (int k = 0; k < K; ++k) sacc[k * 32 + lane] = 0.0f;
+    const int g0 = lane - gl;
+    uint32_t tlo = 0, thi = 0;
     bool active = false;
     if (row < g.N) {
         int64_t rs, re;
         row_range(g, row, rs, re);
         if (re - rs <= g.hub_C) {
             active = true;
-            acc_smem(g, rs, re, gl, lpr, sacc, lane, err);
+            acc_smem(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
         }
     }
-    __syncwarp();
-    const int g0 = grp * lpr;
     RowTail rt;
-    if (active) rt = row_tail(g, row);
-    // lane gl of the group finalises classes k = gl, gl + lpr, ...
+    if (active) {
+        rt = row_tail(g, row);
+        if (rt.aug) {  // the augmentation term lands on the row's own class
+            if (rt.yi < 32) tlo |= 1u << rt.yi;
+            else thi |= 1u << (rt.yi - 32);
+        }
+    }
+    for (int o = lpr >> 1; o > 0; o >>= 1) {
+        tlo |= __shfl_xor_sync(0xffffffffu, tlo, o);
+        thi |= __shfl_xor_sync(0xffffffffu, thi, o);
+    }
+    __syncwarp();
     float ss = 0.0f;
     for (int k = gl; k < K; k += lpr) {
+        const bool hit = (k < 32) ? ((tlo >> k) & 1u) : ((thi >> (k - 32)) & 1u);
+        if (!hit) continue;
         float tot = 0.0f;
-        for (int j = 0; j < lpr; ++j) tot += sacc[k * 32 + g0 + j];
-        if (active) tot = finish_entry(tot, k, rt);
-        ss += tot * tot;
-        sacc[k * 32 + g0] = tot;  // keep the finished value (slot of the group's lane 0)
+        for (int j = 0; j < lpr; ++j) {
+            float *p = sacc + k * 32 + g0 + ((j + gl) & (lpr - 1));
+            tot += *p;
+            *p = 0.0f;
+        }
+        const float v = finish_entry(tot, k, rt);
+        ss += v * v;
+        sacc[k * 32 + lane] = v;  // kept in this lane's own column until it is stored
     }
-    // row 2-norm: sum over the group's lanes in a fixed order
     for (int o = lpr >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    __syncwarp();
     if (!active) return;
     float r = 1.0f;
     bool div = false;
@@ -1226,7 +1278,12 @@ __device__ __forceinline__ void light_rows_smem(const GraphDesc &g, int t, int l
     }
     float *z = g.Z + row * (int64_t)K;
     for (int k = gl; k < K; k += lpr) {
-        const float v = sacc[k * 32 + g0];
+        const bool hit = (k < 32) ? ((tlo >> k) & 1u) : ((thi >> (k - 32)) & 1u);
+        float v = 0.0f;
+        if (hit) {
+            v = sacc[k * 32 + lane];
+            sacc[k * 32 + lane] = 0.0f;
+        }
         z[k] = div ? v / r : v;
     }
 }
@@ -1260,11 +1317,12 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
         float *wa = sacc + warp * kMaxK * 32;
         for (int k = 0; k < K; ++k) wa[k * 32 + lane] = 0.0f;
         __syncwarp();
-        if (ws < we) acc_smem(g, ws, we, lane, 32, wa, lane, err);
+        uint32_t tlo = 0, thi = 0;
+        if (ws < we) acc_smem(g, ws, we, lane, 32, wa, lane, tlo, thi, err);
         __syncwarp();
         for (int k = lane; k < K; k += 32) {
             float tot = 0.0f;
-            for (int j = 0; j < 32; ++j) tot += wa[k * 32 + j];
+            for (int j = 0; j < 32; ++j) tot += wa[k * 32 + ((j + lane) & 31)];
             wtot[warp * kMaxK + k] = tot;
         }
     }
@@ -1322,37 +1380,71 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
+constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
+
+// hub rows: one CTA per chunk
+__global__ void __launch_bounds__(kThreads) k_spmm_hub(Ctx c) {
     extern __shared__ __align__(16) float sacc_all[];
     __shared__ GraphDesc sg;
-    __shared__ int sl[2];
     __shared__ int s_it;
     __shared__ int s_last;
     __shared__ float wtot[kWarps * kMaxK];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
     uint32_t err = 0;
     for (;;) {
-        ItemRef r = next_item(c, 4, &s_it, hub_chunks, H);
-        if (r.kind < 0) break;
-        if (r.kind == 0) {
-            const HubEntry he = c.cb.hubs[r.hub];
-            load_desc_idx(c, he.g, &sg);
-            const int K = sg.K;
-            if (K <= 1) hub_chunk<1>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
-            else if (K <= 2) hub_chunk<2>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
-            else if (K <= 4) hub_chunk<4>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
-            else if (K <= 8) hub_chunk<8>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
-            else hub_chunk<0>(c, sg, he, r.hub, r.local, sacc_all, wtot, &s_last, err);
-        } else {
-            const int t = load_desc(c, r.local, &sg, sl, c.prefix);
-            const int K = sg.K;
-            if (K <= 1) light_rows_reg<1>(sg, t, lane, warp, err);
-            else if (K <= 2) light_rows_reg<2>(sg, t, lane, warp, err);
-            else if (K <= 4) light_rows_reg<4>(sg, t, lane, warp, err);
-            else if (K <= 8) light_rows_reg<8>(sg, t, lane, warp, err);
-            else light_rows_smem(sg, t, lane, warp, sacc_all + warp * kMaxK * 32, err);
+        const int it = cta_claim(&c.cb.cs->ctr[4], &s_it);
+        if ((uint32_t)it >= hub_chunks) break;
+        const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
+        const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
+        const HubEntry he = c.cb.hubs[hub];
+        load_desc_idx(c, he.g, &sg);
+        const int K = sg.K;
+        if (K <= 1) hub_chunk<1>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        else if (K <= 2) hub_chunk<2>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        else if (K <= 4) hub_chunk<4>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        else if (K <= 8) hub_chunk<8>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        else hub_chunk<0>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        if (err) {
+            atomicOr(sg.status, err);
+            err = 0;
+        }
+    }
+}
+
+// light rows: persistent warps, each claiming blocks of rows_per_item rows
+__global__ void __launch_bounds__(kThreads) k_spmm_rows(Ctx c) {
+    extern __shared__ __align__(16) float sacc_all[];
+    __shared__ GraphDesc wd[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *sacc = sacc_all + warp * kMaxK * 32;
+    if (c.cb.kmax > kRegK)
+        for (int i = lane; i < kMaxK * 32; i += 32) sacc[i] = 0.0f;
+    __syncwarp();
+    int cur = -1;
+    uint32_t err = 0;
+    for (;;) {
+        const uint32_t it = warp_claim(&c.cb.cs->ctr[5]);
+        if (it >= (uint32_t)c.items) break;
+        int blk;
+        const int g = warp_item_graph(c, it, blk);
+        if (g != cur) {
+            __syncwarp();
+            warp_load_desc(c, g, &wd[warp]);
+            cur = g;
+        }
+        const GraphDesc &sg = wd[warp];
+        const int lpr = 1 << sg.lpr_log2;
+        const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
+        const int rows_per_round = 32 >> sg.lpr_log2;
+        const int K = sg.K;
+        for (int r0 = 0; r0 < sg.rows_per_item; r0 += rows_per_round) {
+            const int64_t row = (int64_t)blk * sg.rows_per_item + r0 + grp;
+            if (K <= 1) light_row_reg<1>(sg, row, gl, lpr, err);
+            else if (K <= 2) light_row_reg<2>(sg, row, gl, lpr, err);
+            else if (K <= 4) light_row_reg<4>(sg, row, gl, lpr, err);
+            else if (K <= 8) light_row_reg<8>(sg, row, gl, lpr, err);
+            else light_row_smem(sg, row, gl, lpr, sacc, lane, err);
         }
         if (err) {
             atomicOr(sg.status, err);
@@ -1446,15 +1538,25 @@ cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st) {
-    if (blocks <= 0) return cudaSuccess;
-    k_wdeg<<<blocks, kThreads, 0, st>>>(c);
+cudaError_t launch_wdeg(const Ctx &c, int hub_blocks, int row_blocks, cudaStream_t st) {
+    if (hub_blocks > 0) {
+        k_wdeg_hub<<<hub_blocks, kThreads, 0, st>>>(c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (row_blocks > 0) k_wdeg_rows<<<row_blocks, kThreads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+cudaError_t launch_spmm_hub(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_spmm<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    k_spmm_hub<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmm_rows(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    k_spmm_rows<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1471,25 +1573,20 @@ cudaError_t configure_kernels() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+    e = cudaFuncSetAttribute(k_spmm_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
 }
 
-int occupancy_spmm(bool smem_acc) {
+static int occ(const void *f, size_t smem) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmm, kThreads, smem_acc ? kSmemAccBytes : 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem);
     return n > 0 ? n : 1;
 }
 
-int occupancy_scatter(int digit_bits) {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scatter<true>, kThreads, scatter_smem_bytes(1 << digit_bits));
-    return n > 0 ? n : 1;
-}
-
-int occupancy_wdeg() {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_wdeg, kThreads, 0);
-    return n > 0 ? n : 1;
-}
+int occupancy_spmm_rows(bool smem_acc) { return occ((const void *)k_spmm_rows, smem_acc ? kSmemAccBytes : 0); }
+int occupancy_spmm_hub(bool smem_acc) { return occ((const void *)k_spmm_hub, smem_acc ? kSmemAccBytes : 0); }
+int occupancy_wdeg_rows() { return occ((const void *)k_wdeg_rows, 0); }
+int occupancy_wdeg_hub() { return occ((const void *)k_wdeg_hub, 0); }
 
 }  // namespace gee
