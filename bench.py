@@ -43,6 +43,9 @@ WORKLOADS = {
     "batch": dict(desc="4,096 graphs in one launch sequence (CUDA graph): N log-uniform [100, 50,000], mean "
                        "degree U[5,200], SBM or Chung-Lu (gamma 2.1) per graph, K U{2..64}, weights U(0,1], "
                        "all options, seed 4"),
+    "serve": dict(desc="continuous-batching server: Poisson arrivals of graphs from the batch mix (256 distinct "
+                       "graphs) plus 1% large Chung-Lu graphs (N=2M, 100M undirected edges, K=16), pinned host "
+                       "inputs, 64 GiB device budget, 2 compute streams, all options, seed 5"),
 }
 
 
@@ -267,6 +270,95 @@ def batch_arm(args, ws_n, rank, local, dev):
     return 0
 
 
+def serve_arm(args, ws_n, rank, local, dev):
+    import threading
+    import torch
+    import paper_2406_03726_gb300 as gee
+    from synth import batch_specs
+    from synth.torch_batch import batch_graph_torch
+    rng = np.random.default_rng(5 + 1000 * rank)
+    specs = batch_specs(256, seed=5 + 1000 * rank)
+    big = {"index": -1, "N": 2_000_000, "m": 100_000_000, "E": 200_000_000, "K": 16, "kind": "chung_lu",
+           "seed": 77 + rank}
+
+    def to_host(sp):
+        src, dst, w, y = batch_graph_torch(sp, dev)
+        pin = [t.cpu().pin_memory() for t in (src, dst, w, y)]
+        del src, dst, w, y
+        return pin, sp
+
+    pool = [to_host(sp) for sp in specs]
+    big_host = to_host(big)
+    torch.cuda.empty_cache()
+
+    def draw(R):
+        return [big_host if rng.random() < 0.01 else pool[rng.integers(len(pool))] for _ in range(R)]
+
+    def run(reqs, rate):
+        srv = gee.Server(64 << 30, ALL_OPTIONS, max_batch=1024, streams=2)
+        tickets = [None] * len(reqs)
+        t_sub = [0.0] * len(reqs)
+
+        def submitter():
+            t0 = time.perf_counter()
+            t_next = t0
+            for i, ((s_, d_, w_, y_), sp) in enumerate(reqs):
+                if rate:
+                    t_next += rng.exponential(1.0 / rate)
+                    while True:
+                        dt = t_next - time.perf_counter()
+                        if dt <= 0:
+                            break
+                        time.sleep(min(dt, 0.002))
+                t_sub[i] = time.perf_counter()
+                tickets[i] = srv.submit(s_.numpy(), d_.numpy(), w_.numpy(), y_.numpy(), sp["N"], sp["K"])
+
+        th = threading.Thread(target=submitter)
+        t_start = time.perf_counter()
+        th.start()
+        lat = []
+        t_last = t_start
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            res = srv.poll(tickets[i], wait=True)
+            if res is None:
+                raise RuntimeError("request did not complete")
+            lat.append(res[2])
+            t_last = time.perf_counter()
+            srv.release(tickets[i])
+        th.join()
+        st = srv.stats()
+        srv.close()
+        edges = sum(sp["E"] for _, sp in reqs)
+        span = t_last - t_start
+        lat = np.array(lat)
+        return {"requests": len(reqs), "edges": int(edges), "seconds": span, "edges_per_s": edges / span,
+                "req_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "launches": int(st["launches"]),
+                "peak_pool_bytes": int(st["peak_bytes_in_use"]), "pool_bytes": int(st["pool_bytes"])}
+
+    R = max(200, args.steps)
+    run(draw(50), None)                                  # warm-up
+    with ClockSampler(local) as clk:
+        sat = run(draw(R), None)                          # everything at once: saturation
+        r50 = run(draw(R), 0.5 * sat["req_per_s"])
+        r90 = run(draw(R), 0.9 * sat["req_per_s"])
+    line = {"metric": METRIC, "value": sat["edges_per_s"] * ws_n, "unit": UNIT, "n_gpus": ws_n, "steps": R,
+            "warmup": 50, "ms_per_step": 1e3 * sat["seconds"] / R, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serve"]["desc"], "requests_per_run": R,
+                       "parallelism": f"replicas x{ws_n} (independent servers, no collective)"},
+            "serving": {"saturation": sat, "at_50pct": r50, "at_90pct": r90},
+            "e2e": {"value": sat["edges_per_s"], "unit": UNIT,
+                    "h2d_bytes_per_step": int(sat["edges"] * 12 / R), "d2h_bytes_per_step": 0,
+                    "note": "host inputs in, Z resident on the device (the serving contract)"},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def gpu_arm(args):
     import torch
     import paper_2406_03726_gb300 as gee
@@ -277,8 +369,8 @@ def gpu_arm(args):
     if ws_n > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    if args.workload == "batch":
-        rc = batch_arm(args, ws_n, rank, local, dev)
+    if args.workload in ("batch", "serve"):
+        rc = (batch_arm if args.workload == "batch" else serve_arm)(args, ws_n, rank, local, dev)
         if ws_n > 1:
             torch.distributed.destroy_process_group()
         return rc
@@ -444,7 +536,7 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
-        if args.workload == "batch":
+        if args.workload in ("batch", "serve"):
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single graphs only"}))
             return 0
         return reference_arm(args)

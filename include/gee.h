@@ -57,7 +57,10 @@ typedef enum gee_error {
     GEE_ERR_TOO_LARGE = 2, /* N, E or K beyond the limits above */
     GEE_ERR_WORKSPACE = 3, /* workspace NULL, too small, or not 256-byte aligned */
     GEE_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
-    GEE_ERR_DATA = 5       /* (blocking calls only) the device reported GEE_STATUS_* bits */
+    GEE_ERR_DATA = 5,      /* (blocking calls only) the device reported GEE_STATUS_* bits */
+    GEE_ERR_NOMEM = 6,     /* the server's memory budget cannot hold the request (or its pool) */
+    GEE_PENDING = 7,       /* (server) the request has not completed yet */
+    GEE_ERR_STATE = 8      /* (server) unknown ticket, or not allowed in the request's state */
 } gee_error;
 
 /* Device status bits, OR-ed into the status word of a call. */
@@ -232,6 +235,68 @@ int gee_batch_plan_launch(gee_batch_plan *plan, void *stream, uint32_t *d_status
  * and stores the device time of each phase, in ms, into HOST phase_ms[GEE_NUM_PHASES]. */
 int gee_batch_plan_launch_timed(gee_batch_plan *plan, void *stream, float *phase_ms);
 void gee_batch_plan_destroy(gee_batch_plan *plan);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of embedding requests.
+ *
+ * The server owns one device memory pool of `hbm_budget` bytes (allocated once by
+ * gee_server_create) and a worker thread.  Submitted requests are admitted first come,
+ * first served, as soon as their inputs, Z and a workspace fit in the pool; admitted
+ * requests are copied to the device on a copy stream
+ * and gathered into batches that run through the batch path on `streams` compute
+ * streams, so work admitted while other batches run overlaps with them.  A batch's
+ * workspace (the CSR of its graphs) and each request's Z stay resident until the request
+ * is released.  Each request's Z is bit-identical to gee_embed's for the same graph.
+ * Latency = submission to completion of the request's batch on the device.
+ */
+typedef struct gee_server gee_server;
+
+typedef struct gee_server_config {
+    size_t hbm_budget; /* device bytes for inputs, workspaces and Z (>= 1 MiB) */
+    int32_t max_batch; /* most graphs per launch; 0 = 1024 */
+    int32_t streams;   /* concurrent compute streams; 0 = 2 */
+    uint32_t flags;    /* embedding options for every request */
+    int32_t reserved;  /* must be 0 */
+} gee_server_config;
+
+typedef struct gee_request {
+    const int32_t *src, *dst; /* HOST int32 [E]; must stay valid until the request completes
+                                 (pinned memory lets the copy overlap other work) */
+    const float *w;           /* HOST float32 [E] or NULL */
+    const int32_t *labels;    /* HOST int32 [N] */
+    int64_t E;
+    int32_t N, K;
+} gee_request;
+
+typedef struct gee_server_stats {
+    int64_t submitted, completed, queued, running;
+    int64_t launches, edges_done;
+    uint64_t pool_bytes, bytes_in_use, peak_bytes_in_use; /* peak never exceeds pool_bytes */
+    int32_t last_error;                                   /* last launch error (GEE_OK if none) */
+    int32_t reserved;
+} gee_server_stats;
+
+/* Create a server on the current device.  GEE_ERR_NOMEM if the pool cannot be allocated. */
+int gee_server_create(const gee_server_config *cfg, gee_server **server);
+/* Queue a request; *ticket identifies it.  GEE_ERR_NOMEM if it could not fit in the pool
+ * even alone (refused at once). */
+int gee_server_submit(gee_server *server, const gee_request *req, int64_t *ticket);
+/* GEE_OK once done (then *d_Z = its device Z [N][K], *status = its GEE_STATUS_* bits,
+ * *latency_ms = submit-to-done time; each output pointer may be NULL), GEE_PENDING
+ * before.  wait != 0 blocks until done, for at most 120 s (then GEE_PENDING).
+ * GEE_ERR_CUDA if the request's batch failed on the device. */
+int gee_server_poll(gee_server *server, int64_t ticket, int wait, const float **d_Z, uint32_t *status,
+                    double *latency_ms);
+/* Wait for the request and copy its Z to HOST Z_host [N][K]. */
+int gee_server_fetch(gee_server *server, int64_t ticket, float *Z_host);
+/* Drop a request that is still queued (admitted work always completes). */
+int gee_server_cancel(gee_server *server, int64_t ticket);
+/* Free a completed request's resident memory (its Z, and its batch's CSR once every
+ * request of the batch is released). */
+int gee_server_release(gee_server *server, int64_t ticket);
+int gee_server_get_stats(gee_server *server, gee_server_stats *stats);
+/* Stop the worker, wait for the device, free the pool. */
+void gee_server_destroy(gee_server *server);
 
 /* Human-readable text of a gee_error code. */
 const char *gee_strerror(int code);

@@ -8,6 +8,16 @@ only allocate device memory with PyTorch and call it.
 from __future__ import annotations
 
 from ._native import (  # noqa: F401
+    gee_request,
+    gee_server_cancel,
+    gee_server_config,
+    gee_server_create,
+    gee_server_destroy,
+    gee_server_fetch,
+    gee_server_get_stats,
+    gee_server_poll,
+    gee_server_release,
+    gee_server_submit,
     gee_batch_plan_create,
     gee_batch_plan_destroy,
     gee_batch_plan_launch,
@@ -40,6 +50,10 @@ STATUS_INDEX = 1
 STATUS_LABEL = 2
 STATUS_WEIGHT = 4
 STATUS_TIMEOUT = 8
+
+ERR_NOMEM = 6
+PENDING = 7
+ERR_STATE = 8
 
 PHASES = ("memset", "k_prep", "k_offsets_first", "k_scatter_first", "k_count", "k_offsets_final",
           "k_scatter_final", "k_rowscan", "k_hubprep", "k_wdeg_hub", "k_wdeg_rows", "k_spmm_hub", "k_spmm_rows")
@@ -153,3 +167,70 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching server (one device memory pool of `budget` bytes).  Requests are
+    NumPy host arrays (pinned memory is used when given torch pinned tensors); the caller
+    keeps them alive until the request completes."""
+
+    def __init__(self, budget, flags=0, max_batch=0, streams=0):
+        cfg = gee_server_config(int(budget), max_batch, streams, flags, 0)
+        rc, self.handle = gee_server_create(cfg)
+        _check(rc, "gee_server_create")
+        self._keep = {}
+
+    def submit(self, src, dst, w, labels, N, K):
+        E = int(len(src))
+        req = gee_request(_ptr(src), _ptr(dst), _ptr(w), _ptr(labels), E, N, K)
+        rc, ticket = gee_server_submit(self.handle, req)
+        if rc:
+            raise GeeError(rc, "gee_server_submit")
+        self._keep[ticket] = (src, dst, w, labels, N, K)
+        return ticket
+
+    def poll(self, ticket, wait=False):
+        """None while pending, else (device Z address, status bits, latency ms)."""
+        rc, z, st, lat = gee_server_poll(self.handle, ticket, wait)
+        if rc == PENDING:
+            return None
+        _check(rc, "gee_server_poll")
+        return z, st, lat
+
+    def fetch(self, ticket):
+        import numpy as np
+        _, _, _, _, N, K = self._keep[ticket]
+        Z = np.empty((N, K), np.float32)
+        _check(gee_server_fetch(self.handle, ticket, Z), "gee_server_fetch")
+        return Z
+
+    def cancel(self, ticket):
+        rc = gee_server_cancel(self.handle, ticket)
+        if rc == 0:
+            self._keep.pop(ticket, None)
+        return rc
+
+    def release(self, ticket):
+        _check(gee_server_release(self.handle, ticket), "gee_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        rc, st = gee_server_get_stats(self.handle)
+        _check(rc, "gee_server_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            gee_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(a):
+    from ._native import ptr
+    return ptr(a)

@@ -24,6 +24,23 @@ class gee_graph(ctypes.Structure):
                 ("N", ctypes.c_int32), ("K", ctypes.c_int32)]
 
 
+class gee_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class gee_request(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("E", ctypes.c_int64), ("N", ctypes.c_int32), ("K", ctypes.c_int32)]
+
+
+class gee_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("launches", ctypes.c_int64), ("edges_done", ctypes.c_int64),
+                ("pool_bytes", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64),
+                ("peak_bytes_in_use", ctypes.c_uint64), ("last_error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _SIGNATURES = {
     "gee_version": ([], ctypes.c_int),
     "gee_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -41,6 +58,14 @@ _SIGNATURES = {
     "gee_batch_plan_launch": ([_P, _P, _P, ctypes.c_int], ctypes.c_int),
     "gee_batch_plan_launch_timed": ([_P, _P, _P], ctypes.c_int),
     "gee_batch_plan_destroy": ([_P], None),
+    "gee_server_create": ([_P, _P], ctypes.c_int),
+    "gee_server_submit": ([_P, _P, _P], ctypes.c_int),
+    "gee_server_poll": ([_P, _I64, ctypes.c_int, _P, _P, _P], ctypes.c_int),
+    "gee_server_fetch": ([_P, _I64, _P], ctypes.c_int),
+    "gee_server_cancel": ([_P, _I64], ctypes.c_int),
+    "gee_server_release": ([_P, _I64], ctypes.c_int),
+    "gee_server_get_stats": ([_P, _P], ctypes.c_int),
+    "gee_server_destroy": ([_P], None),
     "gee_embed_host": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
 }
 
@@ -193,3 +218,48 @@ def gee_batch_plan_destroy(plan) -> None:
 
 def gee_batch_plan_launch_timed(plan, stream=None, phase_ms=None) -> int:
     return lib().gee_batch_plan_launch_timed(plan, stream_handle(stream), ptr(phase_ms))
+
+
+def gee_server_create(config):
+    """(return code, server handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().gee_server_create(ctypes.byref(config), ctypes.byref(h))
+    return rc, h
+
+
+def gee_server_submit(server, request):
+    """(return code, ticket)."""
+    t = ctypes.c_int64()
+    rc = lib().gee_server_submit(server, ctypes.byref(request), ctypes.byref(t))
+    return rc, t.value
+
+
+def gee_server_poll(server, ticket, wait=False):
+    """(return code, device Z address, status bits, latency in ms)."""
+    z = ctypes.c_void_p()
+    st = ctypes.c_uint32()
+    lat = ctypes.c_double()
+    rc = lib().gee_server_poll(server, ticket, 1 if wait else 0, ctypes.byref(z), ctypes.byref(st), ctypes.byref(lat))
+    return rc, z.value, st.value, lat.value
+
+
+def gee_server_fetch(server, ticket, Z_host) -> int:
+    return lib().gee_server_fetch(server, ticket, ptr(Z_host))
+
+
+def gee_server_cancel(server, ticket) -> int:
+    return lib().gee_server_cancel(server, ticket)
+
+
+def gee_server_release(server, ticket) -> int:
+    return lib().gee_server_release(server, ticket)
+
+
+def gee_server_get_stats(server):
+    st = gee_server_stats()
+    rc = lib().gee_server_get_stats(server, ctypes.byref(st))
+    return rc, st
+
+
+def gee_server_destroy(server) -> None:
+    lib().gee_server_destroy(server)

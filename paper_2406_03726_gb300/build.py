@@ -15,10 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libgee.so")
-SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu", "csrc/gee_static.cu"]
+SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu", "csrc/gee_static.cu", "csrc/gee_server.cu"]
 HEADERS = ["csrc/gee_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                     "-Xcompiler", "-pthread",
                      "-I", os.path.join(ROOT, "include")]
 
 
@@ -62,7 +63,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     for o in objs:
         try:

@@ -401,6 +401,9 @@ const char *gee_strerror(int code) {
         case GEE_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
         case GEE_ERR_CUDA: return "CUDA runtime error";
         case GEE_ERR_DATA: return "the device reported invalid input data (see status bits)";
+        case GEE_ERR_NOMEM: return "the memory budget cannot hold the request";
+        case GEE_PENDING: return "the request has not completed yet";
+        case GEE_ERR_STATE: return "unknown ticket or request state does not allow this";
         default: return "unknown error";
     }
 }
@@ -651,7 +654,10 @@ int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base
         GraphDesc &d = L.descs[g];
         std::memset(&d, 0, sizeof(d));
         plan_params(Shape{graphs[g].E, graphs[g].N, graphs[g].K, graphs[g].w != nullptr}, o, false, d);
-        d.range_tiles = kBatchRangeTiles;  // only changes how work is cut, never the result
+        // ranges of at least 8 tiles (one CTA each, many graphs in flight); never more
+        // ranges than the graph alone would use, so a batch needs no more workspace
+        // than its graphs would separately.  Only how work is cut changes, never Z.
+        d.range_tiles = std::max(kBatchRangeTiles, d.range_tiles);
         d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
         hub_cap += hub_cap_of(d);
         chunk_cap += chunk_cap_of(d);
@@ -700,6 +706,9 @@ int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base
         plan_accumulate(lp, d);
     }
     for (int k = 0; k < kNumPfx; ++k) lp.prefix[k] = L.d_prefix ? L.d_prefix + (size_t)k * (G + 1) : nullptr;
+    // the kernels read a lone graph's descriptor from the launch parameters (g0), not
+    // from the device array
+    if (G == 1) lp.base.g0 = L.descs[0];
     lp.zero_base = cb.cs;
     lp.zero_bytes = zero_bytes;
     return GEE_OK;

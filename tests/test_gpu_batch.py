@@ -110,3 +110,14 @@ def test_embed_batch_one_shot_entry_point(gee):
     assert int(st.abs().sum().item()) == 0
     for g, Zb in zip(graphs, Zs):
         assert_z_matches(Zb.double().cpu().numpy(), oracle.embed_graph(g, ALL), what=g.name)
+
+
+def test_batch_of_one_graph(gee):
+    g = small_mix(1, seed=46)[0]
+    s, d, w, y = dev_graph(g)
+    plan = gee.BatchPlan([(s, d, w, y, g.N, g.K)], ALL)
+    for use_graph in (False, True):
+        Zb = plan.launch(use_graph=use_graph)[0]
+        torch.cuda.synchronize()
+        assert np.array_equal(Zb.cpu().numpy(), gee.embed(s, d, w, g.N, y, g.K, ALL).cpu().numpy())
+    plan.close()
