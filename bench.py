@@ -516,10 +516,15 @@ def load_peaks():
 
 
 def traffic_for(kernel, workload):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if one matches."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary (profiles/traffic.json),
+    or None when there is none or it was taken on a different kernel source."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2406_03726_gb300", "csrc", "gee_kernels.cu")
     try:
         d = json.load(open(p))
+        if d.get("source_sha1") != hashlib.sha1(open(src, "rb").read()).hexdigest():
+            return None
         return d.get(workload, {}).get(kernel)
     except Exception:
         return None
