@@ -136,7 +136,9 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
     d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
-    d.rows_per_item = 4 * (32 >> d.lpr_log2);  // four rounds of a warp's row groups
+    // rows a warp claims at once: whole 32-row blocks sorted by length, or two rows when
+    // the rows are long enough that each takes the whole warp anyway
+    d.rows_per_item = lpr >= 32 ? 2 : 32;
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
     // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
     // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
@@ -313,13 +315,14 @@ int run_plan(const LaunchPlan &lp, const DeviceInfo &dev, cudaStream_t st, Phase
     const bool hubs = cb.hub_cap > 0 && (embed || lp.any_wdeg);
     GEE_PHASE(kPhHubprep, hubs, launch_hubprep(cb, st));
     const int64_t hub_grid_max = cb.hub_cap > 0 ? cb.chunk_cap : 0;
-    const int whub = (int)std::min<int64_t>(lp.any_wdeg ? hub_grid_max : 0, (int64_t)dev.sms * dev.occ_whub);
+    // hub kernels: a grid of at most one CTA per SM (they leave at once when no row is split)
+    const int whub = (int)std::min<int64_t>(lp.any_wdeg ? hub_grid_max : 0, (int64_t)dev.sms);
     const int64_t wrow_items = lp.items[kPfxWRows];
     const int wrows = (int)std::min<int64_t>((wrow_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_wrows);
     GEE_PHASE(kPhWdegHub, whub > 0, launch_wdeg(ctx(kPfxWRows), whub, 0, st));
     GEE_PHASE(kPhWdeg, wrows > 0, launch_wdeg(ctx(kPfxWRows), 0, wrows, st));
     const int sm = lp.smem_acc ? 1 : 0;
-    const int shub = (int)std::min<int64_t>(hub_grid_max, (int64_t)dev.sms * dev.occ_hub[sm]);
+    const int shub = (int)std::min<int64_t>(hub_grid_max, (int64_t)dev.sms * std::min(2, dev.occ_hub[sm]));
     const int64_t row_items = lp.items[kPfxRows];
     const int srows = (int)std::min<int64_t>((row_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_rows[sm]);
     GEE_PHASE(kPhSpmmHub, embed && shub > 0, launch_spmm_hub(ctx(kPfxRows), shub, lp.smem_acc, st));

@@ -176,33 +176,36 @@ __device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
     return (int)min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
 }
 
-// Stream the ids [0, n) of p (16-byte vectors when aligned) through f(value).
+// Stream the ids [0, n) of p through f(value): a scalar head up to the first 16-byte
+// boundary, then 16-byte vectors (8 per thread in flight), then a scalar tail.
 template <class F>
 __device__ __forceinline__ void stream_ids(const int32_t *p, int n, F &&f) {
-    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
-        constexpr int kV = 8;
-        const int nv = n >> 2;
-        for (int base = 0; base < nv; base += kV * kThreads) {
-            int4 v[kV];
+    int head = (int)(((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) >> 2);
+    if ((reinterpret_cast<uintptr_t>(p) & 3u) != 0) head = n;  // not even 4-byte aligned: scalar
+    head = min(head, n);
+    if ((int)threadIdx.x < head) f(ld_stream(p + threadIdx.x));
+    p += head;
+    n -= head;
+    constexpr int kV = 8;
+    const int nv = n >> 2;
+    for (int base = 0; base < nv; base += kV * kThreads) {
+        int4 v[kV];
 #pragma unroll
-            for (int k = 0; k < kV; ++k) {
-                const int vi = base + threadIdx.x + k * kThreads;
-                v[k] = vi < nv ? ld_stream4(p + 4 * vi) : make_int4(0, 0, 0, 0);
-            }
+        for (int k = 0; k < kV; ++k) {
+            const int vi = base + threadIdx.x + k * kThreads;
+            v[k] = vi < nv ? ld_stream4(p + 4 * vi) : make_int4(0, 0, 0, 0);
+        }
 #pragma unroll
-            for (int k = 0; k < kV; ++k) {
-                if (base + (int)threadIdx.x + k * kThreads < nv) {
-                    f(v[k].x);
-                    f(v[k].y);
-                    f(v[k].z);
-                    f(v[k].w);
-                }
+        for (int k = 0; k < kV; ++k) {
+            if (base + (int)threadIdx.x + k * kThreads < nv) {
+                f(v[k].x);
+                f(v[k].y);
+                f(v[k].z);
+                f(v[k].w);
             }
         }
-        if ((int)threadIdx.x < n - 4 * nv) f(ld_stream(p + 4 * nv + threadIdx.x));
-    } else {
-        for (int i = threadIdx.x; i < n; i += kThreads) f(ld_stream(p + i));
     }
+    if ((int)threadIdx.x < n - 4 * nv) f(ld_stream(p + 4 * nv + threadIdx.x));
 }
 
 __global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
@@ -264,13 +267,17 @@ __global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
 
 // k_offsets: for a block of 32 digits, rewrite cnt[r][d] (counts) as the position where
 // range r writes its first element of digit d: dbase[d] + sum_{r' < r} cnt[r'][d], with
-// dbase the exclusive prefix over digits of the totals.  Warp w owns a slice of ranges.
+// dbase the exclusive prefix over digits of the totals.  1024 threads: lane = digit of
+// the block, each of the 32 warps owns a slice of the ranges (8 loads in flight).
+constexpr int kOffThreads = 1024;
+constexpr int kOffWarps = kOffThreads / 32;
+
 template <bool SECOND>
-__global__ void __launch_bounds__(kThreads) k_offsets(Ctx c) {
+__global__ void __launch_bounds__(kOffThreads) k_offsets(Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
-    __shared__ uint32_t s_scan[kWarps];
-    __shared__ uint32_t csum[kWarps][32];
+    __shared__ uint32_t s_red[kOffWarps];
+    __shared__ uint32_t csum[kOffWarps][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     const int bits = SECOND ? sg.fbits : first_bits(sg);
@@ -278,11 +285,15 @@ __global__ void __launch_bounds__(kThreads) k_offsets(Ctx c) {
     uint32_t *cnt = SECOND ? sg.cnt2 : sg.cnt1;
     const uint32_t *tot = SECOND ? sg.hist2 : sg.hist1;
     const int d0 = 32 * b, d = d0 + lane;
-    // prefix of the totals below this digit block
+    // sum of the totals below this digit block
     uint32_t part = 0;
-    for (int i = tid; i < d0; i += kThreads) part += __ldcg(tot + i);
-    uint32_t below;
-    (void)block_excl_scan(part, s_scan, below);
+    for (int i = tid; i < d0; i += kOffThreads) part += __ldcg(tot + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    uint32_t below = 0;
+    for (int w = 0; w < kOffWarps; ++w) below += s_red[w];
     const uint32_t td = d < D ? __ldcg(tot + d) : 0u;
     uint32_t x = td;
 #pragma unroll
@@ -292,17 +303,17 @@ __global__ void __launch_bounds__(kThreads) k_offsets(Ctx c) {
     }
     const uint32_t dbase = below + x - td;
     const int R = sg.ranges;
-    const int chunk = (R + kWarps - 1) / kWarps;
+    const int chunk = (R + kOffWarps - 1) / kOffWarps;
     const int r0 = min(R, warp * chunk), r1 = min(R, r0 + chunk);
     uint32_t s = 0;
     if (d < D) {
         int r = r0;
-        for (; r + 4 <= r1; r += 4) {
-            const uint32_t a0 = __ldcg(cnt + ((size_t)r << bits) + d);
-            const uint32_t a1 = __ldcg(cnt + ((size_t)(r + 1) << bits) + d);
-            const uint32_t a2 = __ldcg(cnt + ((size_t)(r + 2) << bits) + d);
-            const uint32_t a3 = __ldcg(cnt + ((size_t)(r + 3) << bits) + d);
-            s += a0 + a1 + a2 + a3;
+        for (; r + 8 <= r1; r += 8) {
+            uint32_t a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s += a[q];
         }
         for (; r < r1; ++r) s += __ldcg(cnt + ((size_t)r << bits) + d);
     }
@@ -311,7 +322,18 @@ __global__ void __launch_bounds__(kThreads) k_offsets(Ctx c) {
     uint32_t run = dbase;
     for (int w = 0; w < warp; ++w) run += csum[w][lane];
     if (d < D) {
-        for (int r = r0; r < r1; ++r) {
+        int r = r0;
+        for (; r + 8 <= r1; r += 8) {
+            uint32_t a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                cnt[((size_t)(r + q) << bits) + d] = run;
+                run += a[q];
+            }
+        }
+        for (; r < r1; ++r) {
             uint32_t *p = cnt + ((size_t)r << bits) + d;
             const uint32_t v = __ldcg(p);
             *p = run;
@@ -724,11 +746,15 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
     const int lof = s_lo[0], lol = s_lo[1];
     const bool per_segment = (int64_t)(lol - lof + 1) * D2 <= 4 * (int64_t)n;
     if (per_segment) {
+        const int warp = tid >> 5;
+        const int str = (D2 * kWarps <= kMaxDigits) ? D2 : 0;  // private per-warp histograms
+        const int nseg = str ? kWarps * D2 : D2;
+        uint32_t *hw = seg + warp * str;
         for (int l = lof; l <= lol; ++l) {
             const int64_t ps = max((int64_t)__ldcg(lobase + l), e0);
             const int64_t pe = min(l + 1 < D1 ? (int64_t)__ldcg(lobase + l + 1) : sg.E, e0 + n);
             if (pe <= ps) continue;
-            for (int d = tid; d < D2; d += kThreads) seg[d] = 0;
+            for (int d = tid; d < nseg; d += kThreads) seg[d] = 0;
             __syncthreads();
             stream_ids(reinterpret_cast<const int32_t *>(sg.tmpk + ps), (int)(pe - ps), [&](int v) {
                 uint32_t hi = (uint32_t)v >> nb;
@@ -736,11 +762,15 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
                     err |= kStTimeout;
                     hi = 0;
                 }
-                atomicAdd(&seg[hi], 1u);
+                atomicAdd(&hw[hi], 1u);
             });
             __syncthreads();
             for (int d = tid; d < D2; d += kThreads) {
-                const uint32_t v = seg[d];
+                uint32_t v = 0;
+                if (str)
+                    for (int w = 0; w < kWarps; ++w) v += seg[w * D2 + d];
+                else
+                    v = seg[d];
                 if (v) {
                     acc[d] += v;
                     const uint32_t row = ((uint32_t)d << lb) | (uint32_t)l;
@@ -969,6 +999,69 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
     s = t;
 }
 
+// ---- length-sorted row blocks --------------------------------------------------------
+// A warp claims a block of up to 32 rows, sorts them by length class and runs the rows
+// of one class together, each with its own number of lanes: 1 lane for rows of <= 8
+// entries, 2 for <= 16, ..., 32 for rows longer than 128.  The lane count of a row
+// depends only on its length, so its floating-point sum order (and its bits) do not
+// depend on which rows share the block.  Rows longer than the split threshold belong
+// to the hub kernels and are skipped here.
+
+__device__ __forceinline__ uint32_t lanes_log2_for(int64_t len) {
+    uint32_t c = 0;
+    while (c < 5 && ((int64_t)8 << c) < len) ++c;
+    return c;
+}
+
+// ascending bitonic sort of one 32-bit key per lane
+__device__ __forceinline__ uint32_t warp_sort32(uint32_t key, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t other = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            key = (lower == up) ? min(key, other) : max(key, other);
+        }
+    }
+    return key;
+}
+
+constexpr uint32_t kNoRow = 0xffffffffu;
+
+// Sorted (class << 5 | offset) keys of the block's rows; kNoRow for rows to skip.
+__device__ __forceinline__ uint32_t sorted_row_keys(const GraphDesc &g, int64_t base, int nrows, int lane) {
+    uint32_t key = kNoRow;
+    const int64_t row = base + lane;
+    if (lane < nrows && row < g.N) {
+        int64_t rs, re;
+        row_range(g, row, rs, re);
+        if (re - rs <= g.hub_C) key = (lanes_log2_for(re - rs) << 5) | (uint32_t)lane;
+    }
+    return warp_sort32(key, lane);
+}
+
+// Run f(row, lane-in-group, lanes-per-row) over the block, one round per group of rows
+// of a class; every lane of the warp takes part in every round (row = N when idle).
+template <class F>
+__device__ __forceinline__ void for_sorted_rows(const GraphDesc &g, int64_t base, uint32_t sk, int lane, F &&f) {
+    const int nvalid = __popc(__ballot_sync(0xffffffffu, sk != kNoRow));
+    int pos = 0;
+    while (pos < nvalid) {
+        const uint32_t c = __shfl_sync(0xffffffffu, sk, pos) >> 5;
+        const int n_c = __popc(__ballot_sync(0xffffffffu, sk != kNoRow && (sk >> 5) == c));
+        const int lpr = 1 << c, rpr = 32 >> c;
+        const int grp = lane >> c, gl = lane & (lpr - 1);
+        for (int j = 0; j < n_c; j += rpr) {
+            const int idx = pos + j + grp;
+            const uint32_t k = __shfl_sync(0xffffffffu, sk, min(idx, 31));
+            const int64_t row = (idx < pos + n_c) ? base + (int64_t)(k & 31u) : (int64_t)g.N;
+            f(row, gl, lpr);
+        }
+        pos += n_c;
+    }
+}
+
 // hub rows: one CTA per chunk, FP64 partials, the last CTA of the row sums them in order
 __global__ void __launch_bounds__(kThreads) k_wdeg_hub(Ctx c) {
     __shared__ GraphDesc sg;
@@ -978,6 +1071,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg_hub(Ctx c) {
     const int tid = threadIdx.x;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
+    if (hub_chunks == 0) return;  // no row of any graph is long enough to be split
     for (;;) {
         const int it = cta_claim(&c.cb.cs->ctr[3], &s_it);
         if ((uint32_t)it >= hub_chunks) break;
@@ -1036,25 +1130,29 @@ __global__ void __launch_bounds__(kThreads) k_wdeg_rows(Ctx c) {
         }
         const GraphDesc &sg = wd[warp];
         if (!sg.wdeg) continue;
-        const int lpr = 1 << sg.lpr_log2;
-        const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
-        const int rows_per_round = 32 >> sg.lpr_log2;
-        for (int r0 = 0; r0 < sg.rows_per_item; r0 += rows_per_round) {
-            const int64_t row = (int64_t)blk * sg.rows_per_item + r0 + grp;
+        const int64_t base = (int64_t)blk * sg.rows_per_item;
+        const uint32_t sk = sorted_row_keys(sg, base, sg.rows_per_item, lane);
+        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr) {
             float s = 0.f, cc = 0.f;
             bool active = false;
             if (row < sg.N) {
                 int64_t rs, re;
                 row_range(sg, row, rs, re);
-                if (re - rs <= sg.hub_C) {
-                    active = true;
-                    const int64_t a0 = rs & ~(int64_t)3;
-                    for (int64_t b = a0 + 4 * gl; b < re; b += 4 * lpr) {
-                        const float4 v = ld_stream4(sg.val + b);
-                        const float vv[4] = {v.x, v.y, v.z, v.w};
+                active = true;
+                const int64_t a0 = rs & ~(int64_t)3;
+                const int64_t step = 4 * (int64_t)lpr;
+                for (int64_t b = a0 + 4 * gl; b < re; b += 4 * step) {
+                    float vv[16];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (b + q >= rs && b + q < re) neumaier_add(s, cc, vv[q]);
+                    for (int u = 0; u < 4; ++u) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (b + u * step < re) v = ld_stream4(sg.val + b + u * step);
+                        vv[4 * u] = v.x; vv[4 * u + 1] = v.y; vv[4 * u + 2] = v.z; vv[4 * u + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int64_t e = b + (q >> 2) * step + (q & 3);
+                        if (e >= rs && e < re) neumaier_add(s, cc, vv[q]);
                     }
                 }
             }
@@ -1072,7 +1170,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg_rows(Ctx c) {
                 const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
                 write_node(sg, row, (s + cc) + aug, (sg.flags & kOptLap) != 0);
             }
-        }
+        });
     }
 }
 
@@ -1082,30 +1180,35 @@ __global__ void __launch_bounds__(kThreads) k_wdeg_rows(Ctx c) {
 // Accumulate val_ij * s_j into per-lane accumulators for the entries [lo, hi) of a row,
 // this lane being lane `gl` of a group of `gsz` lanes.  Vector loads of 4 entries from
 // 16-byte aligned addresses (col/val are padded by 4 entries at the end).
-template <int KR>
+// kVecs = 16-byte col/val vectors each lane keeps in flight: 4 for rows that take the
+// whole warp, 2 for short rows (fewer masked-off slots)
+template <int KR, int kVecs>
 __device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
                                         float (&acc)[KR], uint32_t &err) {
     const int64_t a0 = lo & ~(int64_t)3;
     const bool has_w = g.val != nullptr && g.w != nullptr;
     const uint32_t N = (uint32_t)g.N;
     const int64_t step = 4 * (int64_t)gsz;
-    for (int64_t b = a0 + 4 * gl; b < hi; b += 2 * step) {
-        const int64_t b2 = b + step;
-        const bool two = b2 < hi;
-        const int4 c0 = ld_stream4(g.col + b);
-        const float4 v0 = has_w ? ld_stream4(g.val + b) : make_float4(1.f, 1.f, 1.f, 1.f);
-        int4 c1 = make_int4(0, 0, 0, 0);
-        float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (two) {
-            c1 = ld_stream4(g.col + b2);
-            v1 = has_w ? ld_stream4(g.val + b2) : make_float4(1.f, 1.f, 1.f, 1.f);
-        }
-        const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    for (int64_t b = a0 + 4 * gl; b < hi; b += kVecs * step) {
+        // kVecs 16-byte vectors of col (and val) in flight per lane, then their gathers
+        int cc[4 * kVecs];
+        float vv[4 * kVecs];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int64_t e = (q < 4 ? b : b2) + (q & 3);
-            if (e >= lo && e < hi && (q < 4 || two)) {
+        for (int u = 0; u < kVecs; ++u) {
+            const int64_t bu = b + u * step;
+            int4 cv = make_int4(0, 0, 0, 0);
+            float4 fv = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (bu < hi) {
+                cv = ld_stream4(g.col + bu);
+                if (has_w) fv = ld_stream4(g.val + bu);
+            }
+            cc[4 * u] = cv.x; cc[4 * u + 1] = cv.y; cc[4 * u + 2] = cv.z; cc[4 * u + 3] = cv.w;
+            vv[4 * u] = fv.x; vv[4 * u + 1] = fv.y; vv[4 * u + 2] = fv.z; vv[4 * u + 3] = fv.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4 * kVecs; ++q) {
+            const int64_t e = b + (q >> 2) * step + (q & 3);
+            if (e >= lo && e < hi) {
                 uint32_t j = (uint32_t)cc[q];
                 if (j >= N) { err |= kStTimeout; continue; }
                 const int2 t = __ldg(g.tab + j);
@@ -1119,29 +1222,33 @@ __device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t 
 
 // Same, into a per-warp shared-memory accumulator sacc[k * 32 + lane] (K up to 64),
 // recording the touched classes in a 64-bit mask (tlo: classes 0-31, thi: 32-63).
+template <int kVecs>
 __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
                                          float *sacc, int lane, uint32_t &tlo, uint32_t &thi, uint32_t &err) {
     const int64_t a0 = lo & ~(int64_t)3;
     const bool has_w = g.val != nullptr && g.w != nullptr;
     const uint32_t N = (uint32_t)g.N;
     const int64_t step = 4 * (int64_t)gsz;
-    for (int64_t b = a0 + 4 * gl; b < hi; b += 2 * step) {
-        const int64_t b2 = b + step;
-        const bool two = b2 < hi;
-        const int4 c0 = ld_stream4(g.col + b);
-        const float4 v0 = has_w ? ld_stream4(g.val + b) : make_float4(1.f, 1.f, 1.f, 1.f);
-        int4 c1 = make_int4(0, 0, 0, 0);
-        float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (two) {
-            c1 = ld_stream4(g.col + b2);
-            v1 = has_w ? ld_stream4(g.val + b2) : make_float4(1.f, 1.f, 1.f, 1.f);
-        }
-        const int cc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    for (int64_t b = a0 + 4 * gl; b < hi; b += kVecs * step) {
+        // kVecs 16-byte vectors of col (and val) in flight per lane, then their gathers
+        int cc[4 * kVecs];
+        float vv[4 * kVecs];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int64_t e = (q < 4 ? b : b2) + (q & 3);
-            if (e >= lo && e < hi && (q < 4 || two)) {
+        for (int u = 0; u < kVecs; ++u) {
+            const int64_t bu = b + u * step;
+            int4 cv = make_int4(0, 0, 0, 0);
+            float4 fv = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (bu < hi) {
+                cv = ld_stream4(g.col + bu);
+                if (has_w) fv = ld_stream4(g.val + bu);
+            }
+            cc[4 * u] = cv.x; cc[4 * u + 1] = cv.y; cc[4 * u + 2] = cv.z; cc[4 * u + 3] = cv.w;
+            vv[4 * u] = fv.x; vv[4 * u + 1] = fv.y; vv[4 * u + 2] = fv.z; vv[4 * u + 3] = fv.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4 * kVecs; ++q) {
+            const int64_t e = b + (q >> 2) * step + (q & 3);
+            if (e >= lo && e < hi) {
                 uint32_t j = (uint32_t)cc[q];
                 if (j >= N) { err |= kStTimeout; continue; }
                 const int2 t = __ldg(g.tab + j);
@@ -1193,7 +1300,8 @@ __device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, i
         row_range(g, row, rs, re);
         if (re - rs <= g.hub_C) {
             active = true;
-            acc_reg<KR>(g, rs, re, gl, lpr, acc, err);
+            if (lpr == 32) acc_reg<KR, 4>(g, rs, re, gl, lpr, acc, err);
+            else acc_reg<KR, 2>(g, rs, re, gl, lpr, acc, err);
         }
     }
 #pragma unroll
@@ -1225,8 +1333,22 @@ __device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, i
 
 // one light row per lane group, 8 < K <= 64: per-lane shared-memory columns.  The
 // accumulator is all-zero between rows; only the classes the row touched are reduced
-// (lane gl of the group owns the classes k = gl mod lpr, reads the group's columns in a
-// rotated order, which is free of bank conflicts) and cleared again.
+// (lane gl of the group owns the classes k = gl mod lpr and visits just the touched ones,
+// reading the group's columns in a rotated order, free of bank conflicts) and cleared.
+__device__ __forceinline__ uint64_t owned_classes(int gl, int lpr) {
+    // bits k with k mod lpr == gl
+    uint64_t m = 0;
+    switch (lpr) {
+        case 1: m = ~0ull; break;
+        case 2: m = 0x5555555555555555ull; break;
+        case 4: m = 0x1111111111111111ull; break;
+        case 8: m = 0x0101010101010101ull; break;
+        case 16: m = 0x0001000100010001ull; break;
+        default: m = 0x0000000100000001ull; break;
+    }
+    return m << gl;
+}
+
 __device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, int gl, int lpr, float *sacc,
                                                int lane, uint32_t &err) {
     const int K = g.K;
@@ -1238,7 +1360,8 @@ __device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, 
         row_range(g, row, rs, re);
         if (re - rs <= g.hub_C) {
             active = true;
-            acc_smem(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
+            if (lpr == 32) acc_smem<4>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
+            else acc_smem<2>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
         }
     }
     RowTail rt;
@@ -1254,10 +1377,10 @@ __device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, 
         thi |= __shfl_xor_sync(0xffffffffu, thi, o);
     }
     __syncwarp();
+    const uint64_t mine = (((uint64_t)thi << 32) | tlo) & owned_classes(gl, lpr);
     float ss = 0.0f;
-    for (int k = gl; k < K; k += lpr) {
-        const bool hit = (k < 32) ? ((tlo >> k) & 1u) : ((thi >> (k - 32)) & 1u);
-        if (!hit) continue;
+    for (uint64_t m = mine; m; m &= m - 1) {
+        const int k = __ffsll((long long)m) - 1;
         float tot = 0.0f;
         for (int j = 0; j < lpr; ++j) {
             float *p = sacc + k * 32 + g0 + ((j + gl) & (lpr - 1));
@@ -1278,9 +1401,8 @@ __device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, 
     }
     float *z = g.Z + row * (int64_t)K;
     for (int k = gl; k < K; k += lpr) {
-        const bool hit = (k < 32) ? ((tlo >> k) & 1u) : ((thi >> (k - 32)) & 1u);
         float v = 0.0f;
-        if (hit) {
+        if ((mine >> k) & 1ull) {
             v = sacc[k * 32 + lane];
             sacc[k * 32 + lane] = 0.0f;
         }
@@ -1305,7 +1427,7 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
         float acc[KR];
 #pragma unroll
         for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
-        if (ws < we) acc_reg<KR>(g, ws, we, lane, 32, acc, err);
+        if (ws < we) acc_reg<KR, 4>(g, ws, we, lane, 32, acc, err);
 #pragma unroll
         for (int k = 0; k < KR; ++k)
             for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
@@ -1318,7 +1440,7 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
         for (int k = 0; k < K; ++k) wa[k * 32 + lane] = 0.0f;
         __syncwarp();
         uint32_t tlo = 0, thi = 0;
-        if (ws < we) acc_smem(g, ws, we, lane, 32, wa, lane, tlo, thi, err);
+        if (ws < we) acc_smem<4>(g, ws, we, lane, 32, wa, lane, tlo, thi, err);
         __syncwarp();
         for (int k = lane; k < K; k += 32) {
             float tot = 0.0f;
@@ -1391,6 +1513,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_hub(Ctx c) {
     __shared__ float wtot[kWarps * kMaxK];
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
+    if (hub_chunks == 0) return;  // no row of any graph is long enough to be split
     uint32_t err = 0;
     for (;;) {
         const int it = cta_claim(&c.cb.cs->ctr[4], &s_it);
@@ -1434,18 +1557,16 @@ __global__ void __launch_bounds__(kThreads) k_spmm_rows(Ctx c) {
             cur = g;
         }
         const GraphDesc &sg = wd[warp];
-        const int lpr = 1 << sg.lpr_log2;
-        const int grp = lane >> sg.lpr_log2, gl = lane & (lpr - 1);
-        const int rows_per_round = 32 >> sg.lpr_log2;
         const int K = sg.K;
-        for (int r0 = 0; r0 < sg.rows_per_item; r0 += rows_per_round) {
-            const int64_t row = (int64_t)blk * sg.rows_per_item + r0 + grp;
+        const int64_t base = (int64_t)blk * sg.rows_per_item;
+        const uint32_t sk = sorted_row_keys(sg, base, sg.rows_per_item, lane);
+        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr) {
             if (K <= 1) light_row_reg<1>(sg, row, gl, lpr, err);
             else if (K <= 2) light_row_reg<2>(sg, row, gl, lpr, err);
             else if (K <= 4) light_row_reg<4>(sg, row, gl, lpr, err);
             else if (K <= 8) light_row_reg<8>(sg, row, gl, lpr, err);
             else light_row_smem(sg, row, gl, lpr, sacc, lane, err);
-        }
+        });
         if (err) {
             atomicOr(sg.status, err);
             err = 0;
@@ -1506,8 +1627,8 @@ cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st) {
 
 cudaError_t launch_offsets(const Ctx &c, int blocks, bool second, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    if (second) k_offsets<true><<<blocks, kThreads, 0, st>>>(c);
-    else k_offsets<false><<<blocks, kThreads, 0, st>>>(c);
+    if (second) k_offsets<true><<<blocks, kOffThreads, 0, st>>>(c);
+    else k_offsets<false><<<blocks, kOffThreads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
