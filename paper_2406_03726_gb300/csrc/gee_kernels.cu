@@ -24,6 +24,7 @@
 #include "gee_internal.cuh"
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 
 namespace gee {
@@ -433,25 +434,36 @@ __device__ __forceinline__ uint32_t look_back8(const uint32_t *lb, int width, in
 //
 // Tiles of 2048 edges, 8 per thread.  While a tile is ranked and scattered, the next tile
 // of the range streams into shared memory by TMA bulk copies.  Warp w ranks tile
-// elements [256 w, 256 w + 256), item i of lane l being element 256 w + 32 i + l: the
-// lanes holding the same digit are found with one ballot per digit bit (all items at
-// once), then a per-warp counter per digit gives each element its rank among the equal
-// digits before it in input order, so the pass is stable.
+// elements [256 w, 256 w + 256), item i of lane l being element 256 w + 32 i + l.  The
+// lanes of a warp holding the same digit are found through a per-warp table of peer
+// masks: every lane ORs its bit into the entry of its digit, reads the entry back, and
+// the lowest lane of the group clears it again (digits above 256 share entries, and one
+// ballot per remaining digit bit separates them).  A per-warp counter per digit then
+// gives each element its rank among the equal digits before it in input order, so the
+// pass is stable.
 //
-// Shared memory (dynamic, sized by the digit count D): stage (3 streams x 2048 words),
-// a work area (per-warp u16 digit counters + tile starts while ranking, then the tile
-// sorted by digit), and the per-digit output positions and running range offsets.
+// Shared memory (dynamic, sized by the digit count D), every part a multiple of 16 bytes:
+//   stage  3 streams x 2048 words (src|packed, dst, weight): TMA destination
+//   tile   the tile sorted by digit: global position, payload, weight (3 x 2048 words)
+//   wcnt   [kWarps][D] u16 per-warp digit counters (apart from the tile for D <= 512,
+//          else sharing its space)
+//   tstart, dglob, run   [D] u32: tile-local start, tile -> global shift, range offset
+//   bins   [kWarps][min(D, 256)] u32 peer masks (zero between items)
 
 constexpr int kStreamWords = kSortTile;                       // one stream = 2048 words
 constexpr size_t kStageBytes = (size_t)3 * kStreamWords * 4;  // src|tmpk, dst, w|tmpw
+constexpr size_t kTileBytes = (size_t)3 * kSortTile * 4;      // sorted pos, payload, weight
+constexpr int kSepDigits = 512;                               // wcnt apart from the tile up to here
+constexpr int kBinDigits = 256;                               // peer-mask entries per warp
 
-__host__ __device__ constexpr size_t scatter_work_bytes(int D) {
-    return ((size_t)D * kWarps * 2 + (size_t)D * 4) > (size_t)3 * kSortTile * 4
-               ? ((size_t)D * kWarps * 2 + (size_t)D * 4)
-               : (size_t)3 * kSortTile * 4;
+__host__ __device__ constexpr size_t scatter_wcnt_bytes(int D) { return (size_t)D * kWarps * 2; }
+__host__ __device__ constexpr size_t scatter_union_bytes(int D) {
+    return D <= kSepDigits ? kTileBytes + ((scatter_wcnt_bytes(D) + 15) & ~(size_t)15)
+                           : (scatter_wcnt_bytes(D) > kTileBytes ? scatter_wcnt_bytes(D) : kTileBytes);
 }
 __host__ __device__ constexpr size_t scatter_smem_bytes(int D) {
-    return kStageBytes + scatter_work_bytes(D) + (size_t)2 * D * 4;
+    return kStageBytes + scatter_union_bytes(D) + (size_t)3 * D * 4 +
+           (size_t)kWarps * (D < kBinDigits ? D : kBinDigits) * 4;
 }
 
 template <bool FINAL>
@@ -474,6 +486,36 @@ __device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e
     return ok ? 1 : 0;
 }
 
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+// One element of a tile -> (digit, payload, weight).  Source ids >= N count as 0 (k_prep
+// flags them and counts them as 0 too); out-of-range targets are flagged and become 0.
+// Weights are checked by the pass that writes the CSR.
+template <bool FINAL>
+__device__ __forceinline__ void scatter_item(bool coo, uint32_t a, uint32_t b, float x, uint32_t N, int lb, int nb,
+                                             uint32_t nmask, uint32_t dmask, bool has_w, bool lap, uint32_t &key,
+                                             uint32_t &pay, uint32_t &err) {
+    if (coo) {
+        const uint32_t s = a < N ? a : 0u;
+        uint32_t d = b;
+        if (d >= N) {
+            err |= kStIndex;
+            d = 0;
+        }
+        if (FINAL) {
+            key = s;
+            pay = d;
+        } else {
+            key = s & ((1u << lb) - 1u);
+            pay = ((s >> lb) << nb) | d;
+        }
+    } else {
+        key = (a >> nb) & dmask;  // < D for every packed value the first pass writes
+        pay = a & nmask;
+    }
+    if (FINAL && has_w && (!finite_f(x) || (lap && x < 0.0f))) err |= kStWeight;
+}
+
 template <bool FINAL>
 __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -489,8 +531,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
     const bool coo = !FINAL || sg.npass == 1;
     const int bits = FINAL ? sg.fbits : sg.lbits;
     const int D = 1 << bits;
+    const int BD = D < kBinDigits ? D : kBinDigits;
+    const int bbits = bits < 8 ? bits : 8;
+    const uint32_t bmask = (uint32_t)BD - 1u;
+    const bool sep = D <= kSepDigits;
     const int nb = sg.nbits, lb = sg.lbits;
     const uint32_t nmask = (1u << nb) - 1u;  // nb <= 21
+    const uint32_t dmask = (uint32_t)D - 1u;
     const bool has_w = sg.w != nullptr;
     const bool lap = (sg.flags & kOptLap) != 0;
     const uint32_t N = (uint32_t)sg.N;
@@ -498,14 +545,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
     const uint32_t *offs = (FINAL && sg.npass == 2) ? sg.cnt2 : sg.cnt1;
 
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
-    unsigned char *work = smem + kStageBytes;
-    uint16_t *wcnt = reinterpret_cast<uint16_t *>(work);                  // [kWarps][D]
-    uint32_t *tstart = reinterpret_cast<uint32_t *>(work + (size_t)D * kWarps * 2);  // [D]
-    uint32_t *skey = reinterpret_cast<uint32_t *>(work);                  // sorted tile
-    uint32_t *spay = skey + kSortTile;
+    unsigned char *uni = smem + kStageBytes;
+    uint32_t *spos = reinterpret_cast<uint32_t *>(uni);  // sorted tile
+    uint32_t *spay = spos + kSortTile;
     float *sw = reinterpret_cast<float *>(spay + kSortTile);
-    uint32_t *dglob = reinterpret_cast<uint32_t *>(work + scatter_work_bytes(D));  // [D]
-    uint32_t *run = dglob + D;                                            // [D]
+    uint16_t *wcnt = reinterpret_cast<uint16_t *>(sep ? uni + kTileBytes : uni);  // [kWarps][D]
+    uint32_t *tstart = reinterpret_cast<uint32_t *>(uni + scatter_union_bytes(D));
+    uint32_t *dglob = tstart + D;
+    uint32_t *run = dglob + D;
+    uint32_t *bins = run + D;  // [kWarps][BD]
+    uint16_t *mycnt = wcnt + warp * D;
+    uint32_t *mybins = bins + warp * BD;
 
     const int dpt = (D + kThreads - 1) / kThreads;
     const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
@@ -519,123 +569,96 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
         mbar_init(&bar, 1);
         s_staged = scatter_issue_stage<FINAL>(sg, r0, min(rn, kSortTile), stage, &bar);
     }
+    for (int i = tid; i < kWarps * BD; i += kThreads) bins[i] = 0u;
     for (int d = dlo; d < dhi; ++d) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
+    __syncthreads();
     uint32_t parity = 0;
+    const unsigned lt = lanemask_lt();
 
     for (int ti = 0; ti < ntiles; ++ti) {
         const int64_t e0 = r0 + (int64_t)ti * kSortTile;
         const int n = min(kSortTile, rn - ti * kSortTile);
-        __syncthreads();  // the previous tile's write-out is done: its sorted buffer is dead
-        for (int i = tid; i < kWarps * D; i += kThreads) wcnt[i] = 0;
-        __syncthreads();  // counters zeroed, s_staged of this tile visible
-        const int staged = s_staged;
+        const int staged = s_staged;  // written before the last CTA barrier
         if (staged) {
             if (!mbar_wait(&bar, parity)) err |= kStTimeout;
             parity ^= 1u;
         }
 
-        // ---- load the 8 elements of this thread (stage, or global for the tail)
-        const int nst = staged ? (n & ~3) : 0;
+        // ---- the 8 elements of this thread (stage, or global for the tail)
         uint32_t key[kSortItems], pay[kSortItems];
         float wv[kSortItems];
         const int wbase = warp * (32 * kSortItems);
-        if (coo) {
-            const uint32_t lm = (1u << lb) - 1u;
+        if (staged && n == kSortTile) {
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i) {
                 const int idx = wbase + i * 32 + lane;
-                key[i] = 0xffffffffu;
-                pay[i] = 0;
-                wv[i] = 1.0f;
-                if (idx < n) {
-                    uint32_t s, d;
-                    float x = 1.0f;
-                    if (idx < nst) {
-                        s = stage[idx];
-                        d = stage[kStreamWords + idx];
-                        if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
-                    } else {
-                        s = (uint32_t)ld_stream(sg.src + e0 + idx);
-                        d = (uint32_t)ld_stream(sg.dst + e0 + idx);
-                        if (has_w) x = ld_stream(sg.w + e0 + idx);
-                    }
-                    if (s >= N) { err |= kStIndex; s = 0; }
-                    if (d >= N) { err |= kStIndex; d = 0; }
-                    if (has_w && (!finite_f(x) || (lap && x < 0.0f))) err |= kStWeight;
-                    if (FINAL) {
-                        key[i] = s;
-                        pay[i] = d;
-                    } else {
-                        key[i] = s & lm;
-                        pay[i] = ((s >> lb) << nb) | d;
-                    }
-                    wv[i] = x;
-                }
+                const uint32_t a = stage[idx];
+                const uint32_t b = coo ? stage[kStreamWords + idx] : 0u;
+                wv[i] = has_w ? __uint_as_float(stage[2 * kStreamWords + idx]) : 1.0f;
+                scatter_item<FINAL>(coo, a, b, wv[i], N, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i], err);
             }
         } else {
+            const int nst = staged ? (n & ~3) : 0;
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i) {
                 const int idx = wbase + i * 32 + lane;
-                key[i] = 0xffffffffu;
+                key[i] = kNoKey;
                 pay[i] = 0;
                 wv[i] = 1.0f;
                 if (idx < n) {
-                    uint32_t pk;
+                    uint32_t a, b = 0;
                     float x = 1.0f;
                     if (idx < nst) {
-                        pk = stage[idx];
+                        a = stage[idx];
+                        if (coo) b = stage[kStreamWords + idx];
                         if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
+                    } else if (coo) {
+                        a = (uint32_t)ld_stream(sg.src + e0 + idx);
+                        b = (uint32_t)ld_stream(sg.dst + e0 + idx);
+                        if (has_w) x = ld_stream(sg.w + e0 + idx);
                     } else {
-                        pk = ld_stream(sg.tmpk + e0 + idx);
+                        a = ld_stream(sg.tmpk + e0 + idx);
                         if (has_w) x = ld_stream(sg.tmpw + e0 + idx);
                     }
-                    uint32_t hi = pk >> nb;
-                    uint32_t d = pk & nmask;
-                    if (hi >= (uint32_t)D || d >= N) {  // only after an earlier failure
-                        err |= kStTimeout;
-                        hi &= (uint32_t)(D - 1);
-                        d = 0;
-                    }
-                    key[i] = hi;
-                    pay[i] = d;
                     wv[i] = x;
+                    scatter_item<FINAL>(coo, a, b, x, N, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i], err);
                 }
             }
         }
-        __syncthreads();  // stage consumed
+        __syncthreads();  // A: stage consumed; the previous tile's write-out is done
 
         // ---- start streaming the next tile of this range
         if (tid == 0 && ti + 1 < ntiles)
             s_staged = scatter_issue_stage<FINAL>(sg, e0 + kSortTile, min(kSortTile, rn - (ti + 1) * kSortTile),
                                                   stage, &bar);
 
-        // ---- lanes with equal digits: one ballot per digit bit, all items interleaved
-        unsigned peers[kSortItems];
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) peers[i] = __ballot_sync(0xffffffffu, key[i] != 0xffffffffu);
-        for (int b = 0; b < bits; ++b) {
-#pragma unroll
-            for (int i = 0; i < kSortItems; ++i) {
-                const bool bit = (key[i] >> b) & 1u;
-                const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                peers[i] &= bit ? bal : ~bal;
-            }
-        }
-        // ---- stable rank within the warp: per-warp counter of each digit, items in order
-        const unsigned lt = lanemask_lt();
-        uint16_t *mycnt = wcnt + warp * D;
+        // ---- stable rank within the warp: peer masks, then a per-warp counter per digit
+        for (int i = lane; i < D / 2; i += 32) reinterpret_cast<uint32_t *>(mycnt)[i] = 0u;
+        __syncwarp();
         uint32_t rank[kSortItems];
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             const uint32_t d = key[i];
-            const bool valid = d != 0xffffffffu;
+            const bool valid = d != kNoKey;
+            uint32_t *bin = mybins + (d & bmask);
+            if (valid) atomicOr(bin, 1u << lane);
+            __syncwarp();
+            uint32_t peers = valid ? *bin : 0u;
+            for (int b = bbits; b < bits; ++b) {  // digits that share a peer-mask entry
+                const bool bit = (d >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
             const uint32_t before = valid ? (uint32_t)mycnt[d] : 0u;
             __syncwarp();
-            if (valid && (peers[i] & lt) == 0u) mycnt[d] = (uint16_t)(before + __popc(peers[i]));
+            if (valid && (peers & lt) == 0u) {
+                mycnt[d] = (uint16_t)(before + __popc(peers));
+                *bin = 0u;
+            }
             __syncwarp();
-            rank[i] = before + __popc(peers[i] & lt);
+            rank[i] = before + __popc(peers & lt);
         }
-        __syncthreads();
+        __syncthreads();  // B
 
         // ---- per digit: warp offsets, tile counts, tile-local starts, global positions
         uint32_t tcount[8];  // counts of the owned digits (dpt <= 8)
@@ -656,8 +679,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
             loc += sum;
         }
         {
-            uint32_t tot;
-            uint32_t tr = block_excl_scan(loc, s_scan, tot);
+            uint32_t x = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane == 31) s_scan[warp] = x;
+            __syncthreads();  // S
+            uint32_t tr = x - loc;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) tr += (w < warp) ? s_scan[w] : 0u;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int d = dlo + j;
@@ -669,40 +701,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // C
 
-        // ---- tile-local slot of each element (registers), then scatter into shared memory
+        // ---- tile-local slot of each element, then the sorted tile with global positions
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i)
+            if (key[i] != kNoKey) rank[i] += tstart[key[i]] + mycnt[key[i]];
+        if (!sep) __syncthreads();  // the counters share the sorted tile's space
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            if (key[i] != 0xffffffffu) rank[i] += tstart[key[i]] + wcnt[warp * D + key[i]];
-        }
-        __syncthreads();  // counters dead: the sorted tile reuses their space
-#pragma unroll
-        for (int i = 0; i < kSortItems; ++i) {
-            if (key[i] != 0xffffffffu) {
+            if (key[i] != kNoKey) {
                 const uint32_t s = rank[i];
-                skey[s] = key[i];
+                spos[s] = dglob[key[i]] + s;
                 spay[s] = pay[i];
                 sw[s] = wv[i];
             }
         }
-        __syncthreads();
+        __syncthreads();  // E
 
         // ---- write out: consecutive sorted slots of one digit go to consecutive addresses
+        uint32_t *outk = FINAL ? reinterpret_cast<uint32_t *>(sg.col) : sg.tmpk;
+        float *outw = FINAL ? sg.val : sg.tmpw;
 #pragma unroll 4
         for (int s = tid; s < n; s += kThreads) {
-            const uint32_t pos = dglob[skey[s]] + (uint32_t)s;
+            const uint32_t pos = spos[s];
             if (pos >= E32) {
                 err |= kStTimeout;
                 continue;
             }
-            if (FINAL) {
-                sg.col[pos] = (int32_t)spay[s];
-                if (has_w) sg.val[pos] = sw[s];
-            } else {
-                sg.tmpk[pos] = spay[s];
-                if (has_w) sg.tmpw[pos] = sw[s];
-            }
+            outk[pos] = spay[s];
+            if (has_w) outw[pos] = sw[s];
         }
     }
     if (err) atomicOr(&s_err, err);
@@ -1632,11 +1660,17 @@ cudaError_t launch_offsets(const Ctx &c, int blocks, bool second, cudaStream_t s
     return cudaGetLastError();
 }
 
-size_t scatter_smem(int max_digit_bits) { return scatter_smem_bytes(1 << max_digit_bits); }
+// Shared memory for every digit count up to 2^max_digit_bits (the layout is not monotone
+// in D: the counters stop having their own space above kSepDigits).
+size_t scatter_smem(int max_digit_bits) {
+    size_t m = 0;
+    for (int b = 1; b <= max_digit_bits; ++b) m = std::max(m, scatter_smem_bytes(1 << b));
+    return m;
+}
 
 cudaError_t launch_scatter(const Ctx &c, int blocks, bool final_pass, int max_digit_bits, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    const size_t smem = scatter_smem_bytes(1 << max_digit_bits);
+    const size_t smem = scatter_smem(max_digit_bits);
     if (final_pass) k_scatter<true><<<blocks, kThreads, smem, st>>>(c);
     else k_scatter<false><<<blocks, kThreads, smem, st>>>(c);
     return cudaGetLastError();
@@ -1689,7 +1723,7 @@ cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32
 }
 
 cudaError_t configure_kernels() {
-    const int big = (int)scatter_smem_bytes(kMaxDigits);
+    const int big = (int)scatter_smem(kMaxDigitBits);
     cudaError_t e = cudaFuncSetAttribute(k_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
