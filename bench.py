@@ -5,9 +5,12 @@ label counts and checks, CSR build (radix sort by source), degrees and node tabl
 label-gather product with the fused epilogue.  Inputs are resident in HBM; L2 is flushed
 (256 MiB write) before every timed step, outside the timed interval.
 
-Prints ONE JSON line (rank 0).  Keys follow the driver's contract; `roofline` describes
-the dominant kernel (per-kernel CUDA-event times from gee_embed_timed over the timed
-steps), `cpu_baseline` times the FP64 oracle on this host.
+The timed steps call gee_embed, the public entry point (from its third call with the
+same arguments it replays a cached CUDA graph of its kernels).  Prints ONE JSON line
+(rank 0); `roofline` describes the dominant kernel, from per-kernel CUDA-event times of
+gee_embed_timed calls run right after the timed steps (events between kernels would add
+a few microseconds to every timed step), and `cpu_baseline` times the FP64 oracle on
+this host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sbm10k|sbm2k|cl600k]
   python bench.py --impl reference ...     (the oracle arm)
@@ -31,6 +34,7 @@ METRIC = "GEE edges/s and % HBM roofline (all options on); p50/p99 served latenc
 UNIT = "edges/s"
 ALL_OPTIONS = 7
 L2_FLUSH_BYTES = 256 << 20
+KERNEL_TIMING_STEPS = 50
 
 WORKLOADS = {
     "sbm10k": dict(desc="SBM N=10,000, K=3, priors [0.2,0.3,0.5], p_in 0.13, p_out 0.10 "
@@ -394,14 +398,21 @@ def gpu_arm(args):
 
     for _ in range(max(args.warmup, 3)):
         step_plain()
+        # the timed call is the one the timed region repeats: its first call launches
+        # directly, the second captures its launch graph, later ones replay it
+        rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
     torch.cuda.synchronize()
     if int(status.item()) != 0:
         raise RuntimeError(f"device status {int(status.item())}")
 
-    # ---- timed region: K steps, each bracketed by CUDA events on the launch stream
+    # ---- timed region: K steps of the public call, each bracketed by CUDA events on the
+    # launch stream (from the third call on, gee_embed replays its cached launch graph)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_kt = min(args.steps, KERNEL_TIMING_STEPS)
     phase_sum = np.zeros_like(phase)
     phase_cnt = np.zeros_like(phase)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws_n > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -409,8 +420,15 @@ def gpu_arm(args):
         for i in range(args.steps):
             flush.fill_(float(i))               # L2 flush, outside the timed interval
             ev[i][0].record(stream)
-            rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
+            step_plain()
             ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        # ---- kernel timing, right after: the same call with CUDA events between its
+        # kernels (gee_embed_timed), which the timed steps leave out because each event
+        # pair adds a few microseconds to the step
+        for i in range(n_kt):
+            flush.fill_(float(i))
+            rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
             if rc:
                 raise RuntimeError(gee.gee_strerror(rc))
             ok = phase >= 0
@@ -446,12 +464,14 @@ def gpu_arm(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"], "traffic": traffic_for(dom, args.workload),
-                "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel}
+                "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel,
+                "kernel_timing": f"CUDA events between the kernels of gee_embed_timed, {n_kt} L2-flushed "
+                                 "calls right after the timed steps, same process and clock sampling"}
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     e2e = e2e_measure(gee, g, dev, stream, opts, args)
 
-    launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))
+    launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))  # per step
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

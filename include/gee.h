@@ -44,6 +44,9 @@ extern "C" {
 #define GEE_LAPLACIAN 2u
 #define GEE_CORRELATION 4u
 #define GEE_ALL_OPTIONS 7u
+/* Not an option of the method: gee_embed launches its kernels one by one instead of
+ * replaying a cached CUDA graph (see gee_embed). */
+#define GEE_NO_GRAPH_CACHE 0x100u
 
 /* Supported sizes. */
 #define GEE_MAX_N (1 << 21)
@@ -109,17 +112,30 @@ size_t gee_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const g
  * degrees D (after A + I) and the node table s_j = D_jj^-1/2 / n_{y_j}; the label-gather
  * product with the augmentation term, the D_ii^-1/2 scaling and the row 2-norm fused
  * into its epilogue.  Deterministic: the same input gives bit-identical Z.
+ *
+ * Launch cache: the second call with the same arguments (device, every pointer, E, N,
+ * K, opts, workspace_bytes) captures the call's kernel sequence into a CUDA graph, and
+ * later such calls replay it with one launch instead of about a dozen, on `stream`.
+ * The graph re-runs every kernel and reads the inputs afresh; only the host launch
+ * work is saved.  The library keeps up to 16 graphs (least recently used goes first);
+ * gee_graph_cache_clear() frees them.  GEE_NO_GRAPH_CACHE in opts->flags turns it off.
  */
 int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
               const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
               void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status);
+
+/* Destroys the CUDA graphs cached by gee_embed (all devices).  Not to be called while
+ * another thread is inside gee_embed.  Returns GEE_OK or GEE_ERR_CUDA. */
+int gee_graph_cache_clear(void);
 
 /*
  * gee_embed_timed -- gee_embed with CUDA events recorded on `stream` between its launch
  * phases; waits for the stream and stores the device time of each phase, in
  * milliseconds, into the HOST array phase_ms[GEE_NUM_PHASES] (-1 for a phase that
  * launched nothing).  For measurement only: the work and the result are those of
- * gee_embed.  Phases, in launch order:
+ * gee_embed, and it uses the same launch cache (the cached graph of a timed call holds
+ * the events as event-record nodes, so replays are timed phase by phase too).  Phases,
+ * in launch order:
  *   0 workspace memset, 1 k_prep (label counts, checks, first-digit histograms per
  *   range), 2 k_offsets (first pass), 3 k_scatter first pass (graphs with more than
  *   2^11 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final

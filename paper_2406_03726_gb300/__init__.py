@@ -31,6 +31,7 @@ from ._native import (  # noqa: F401
     gee_embed,
     gee_embed_host,
     gee_embed_static,
+    gee_graph_cache_clear,
     gee_embed_timed,
     gee_host_workspace_size,
     gee_opts,
@@ -45,6 +46,7 @@ DIAG_AUG = 1
 LAPLACIAN = 2
 CORRELATION = 4
 ALL_OPTIONS = 7
+NO_GRAPH_CACHE = 0x100
 
 STATUS_INDEX = 1
 STATUS_LABEL = 2

@@ -52,6 +52,7 @@ _SIGNATURES = {
                       ctypes.c_int),
     "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
     "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "gee_graph_cache_clear": ([], ctypes.c_int),
     "gee_batch_workspace_size": ([_P, _I32, _P], _SZ),
     "gee_embed_batch": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
     "gee_batch_plan_create": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
@@ -181,6 +182,10 @@ def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_b
 def gee_embed_static(src, dst, w, E, N, labels, K, opts, Z, stream=None, d_status=None) -> int:
     return lib().gee_embed_static(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
                                   stream_handle(stream), ptr(d_status))
+
+
+def gee_graph_cache_clear() -> int:
+    return lib().gee_graph_cache_clear()
 
 
 def make_graphs(items):

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -276,12 +277,30 @@ enum Phase {
 struct PhaseEvents {
     cudaEvent_t ev[kNumPhases + 1];
     bool ran[kNumPhases];
+    bool external = false;  // being captured into a graph: record as event nodes
 };
 
 inline int mark(PhaseEvents *pe, int ph, cudaStream_t st) {
     if (!pe) return GEE_OK;
-    return cuda_check(cudaEventRecord(pe->ev[ph], st));
+    return cuda_check(pe->external ? cudaEventRecordWithFlags(pe->ev[ph], st, cudaEventRecordExternal)
+                                   : cudaEventRecord(pe->ev[ph], st));
 }
+
+int create_events(PhaseEvents &pe) {
+    for (int i = 0; i <= kNumPhases; ++i)
+        if (cudaEventCreate(&pe.ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(pe.ev[j]);
+            return GEE_ERR_CUDA;
+        }
+    return GEE_OK;
+}
+
+void destroy_events(PhaseEvents &pe) {
+    for (int i = 0; i <= kNumPhases; ++i) cudaEventDestroy(pe.ev[i]);
+}
+
+// Receives the events of a timed call once its work is enqueued.
+using PhaseSink = std::function<int(const PhaseEvents &)>;
 
 #define GEE_PHASE(ph, cond, launch)                  \
     do {                                             \
@@ -422,9 +441,113 @@ size_t gee_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const g
 
 namespace gee {
 namespace {
+
+// ---- launch-graph cache of gee_embed ------------------------------------------------
+// An argument set seen once launches directly and is remembered; the second call with
+// it captures the launch sequence (kernels, memset, status copy) on a private stream
+// and instantiates it; later calls replay the executable graph with one launch.
+struct EmbedKey {
+    int device;
+    const void *src, *dst, *w, *labels, *Z, *ws, *status;
+    int64_t E;
+    int32_t N, K;
+    gee_opts o;
+    size_t ws_bytes;
+    bool timed;  // gee_embed_timed: the graph records the phase events
+    bool operator==(const EmbedKey &b) const {
+        return device == b.device && src == b.src && dst == b.dst && w == b.w && labels == b.labels && Z == b.Z &&
+               ws == b.ws && status == b.status && E == b.E && N == b.N && K == b.K && o.flags == b.o.flags &&
+               o.hub_threshold == b.o.hub_threshold && o.lanes_per_row == b.o.lanes_per_row &&
+               ws_bytes == b.ws_bytes && timed == b.timed;
+    }
+};
+
+struct GraphCacheEntry {
+    EmbedKey key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;  // null: seen once, not captured yet
+    uint64_t used = 0;
+    PhaseEvents pe;        // timed entries: the events the graph records
+    bool have_pe = false;
+};
+
+constexpr size_t kGraphCacheSize = 16;
+std::mutex g_cache_mu;
+std::vector<GraphCacheEntry> *g_cache = nullptr;  // never freed: no CUDA calls at exit
+uint64_t g_cache_clock = 0;
+
+void drop_entry(GraphCacheEntry &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    if (e.have_pe) destroy_events(e.pe);
+    e.exec = nullptr;
+    e.graph = nullptr;
+    e.have_pe = false;
+}
+
+// Enqueue fn(stream, events) for `key`: directly (with the caller's events pe), or
+// through the cached graph (timed keys: with the entry's own events, captured as event
+// nodes).  A timed call's sink then gets the events that were used, under the lock.
+template <class F>
+int launch_cached(const EmbedKey &key, cudaStream_t st, F &&fn, PhaseEvents *pe, const PhaseSink *sink) {
+    auto direct = [&]() -> int {
+        GEE_TRY(fn(st, pe));
+        return (pe && sink) ? (*sink)(*pe) : GEE_OK;
+    };
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!g_cache) g_cache = new std::vector<GraphCacheEntry>();
+    GraphCacheEntry *hit = nullptr;
+    for (auto &e : *g_cache)
+        if (e.key == key) hit = &e;
+    if (!hit) {  // first sighting: remember it (evicting the least recently used)
+        if (g_cache->size() >= kGraphCacheSize) {
+            auto lru = g_cache->begin();
+            for (auto it = g_cache->begin(); it != g_cache->end(); ++it)
+                if (it->used < lru->used) lru = it;
+            drop_entry(*lru);
+            g_cache->erase(lru);
+        }
+        GraphCacheEntry e;
+        e.key = key;
+        e.used = ++g_cache_clock;
+        g_cache->push_back(e);
+        return direct();
+    }
+    hit->used = ++g_cache_clock;
+    if (!hit->exec) {
+        if (key.timed && !hit->have_pe) {
+            GEE_TRY(create_events(hit->pe));
+            hit->have_pe = true;
+        }
+        cudaStream_t cap = nullptr;
+        GEE_TRY(cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)));
+        int rc = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (rc == GEE_OK) {
+            hit->pe.external = true;
+            const int run_rc = fn(cap, key.timed ? &hit->pe : nullptr);
+            hit->pe.external = false;
+            cudaGraph_t graph = nullptr;
+            const int end_rc = cuda_check(cudaStreamEndCapture(cap, &graph));
+            rc = run_rc != GEE_OK ? run_rc : end_rc;
+            if (rc == GEE_OK) rc = cuda_check(cudaGraphInstantiate(&hit->exec, graph, 0));
+            if (rc == GEE_OK) hit->graph = graph;
+            else if (graph) cudaGraphDestroy(graph);
+        }
+        cudaStreamDestroy(cap);
+        if (rc != GEE_OK) {  // capture is unavailable here: launch directly
+            hit->exec = nullptr;
+            cudaGetLastError();
+            return direct();
+        }
+    }
+    GEE_TRY(cuda_check(cudaGraphLaunch(hit->exec, st)));
+    return (key.timed && sink) ? (*sink)(hit->pe) : GEE_OK;
+}
+
 int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
-               size_t workspace_bytes, void *stream, uint32_t *d_status, PhaseEvents *pe) {
+               size_t workspace_bytes, void *stream, uint32_t *d_status, PhaseEvents *pe,
+               const PhaseSink *sink) {
     GEE_TRY(check_shape(E, N, K));
     GEE_TRY(check_inputs(d_src, d_dst, E, N, d_labels));
     if (N > 0 && !d_Z) return GEE_ERR_ARG;
@@ -432,11 +555,12 @@ int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int
     GEE_TRY(check_opts(o));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (N == 0) {
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
         if (pe) {
             std::memset(pe->ran, 0, sizeof(pe->ran));
             for (int i = 0; i <= kNumPhases; ++i) GEE_TRY(cuda_check(cudaEventRecord(pe->ev[i], st)));
+            if (sink) GEE_TRY((*sink)(*pe));
         }
-        if (d_status) return cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st));
         return GEE_OK;
     }
     DeviceInfo dev;
@@ -451,10 +575,36 @@ int embed_impl(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int
     p.d.w = d_w;
     p.d.y = d_labels;
     p.d.Z = d_Z;
-    GEE_TRY(run_single(p, dev, st, pe, true));
-    if (d_status)
-        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
-    return GEE_OK;
+    auto enqueue = [&](cudaStream_t s2, PhaseEvents *pe2) -> int {
+        GEE_TRY(run_single(p, dev, s2, pe2, true));
+        if (d_status)
+            GEE_TRY(cuda_check(
+                cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s2)));
+        return GEE_OK;
+    };
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GEE_TRY(cuda_check(cudaStreamIsCapturing(st, &cs)));
+    if ((o.flags & GEE_NO_GRAPH_CACHE) || cs != cudaStreamCaptureStatusNone) {
+        GEE_TRY(enqueue(st, pe));
+        return (pe && sink) ? (*sink)(*pe) : GEE_OK;
+    }
+    EmbedKey key;
+    std::memset(&key, 0, sizeof(key));
+    cudaGetDevice(&key.device);
+    key.src = d_src;
+    key.dst = d_dst;
+    key.w = d_w;
+    key.labels = d_labels;
+    key.Z = d_Z;
+    key.ws = d_workspace;
+    key.status = d_status;
+    key.E = E;
+    key.N = N;
+    key.K = K;
+    key.o = o;
+    key.ws_bytes = workspace_bytes;
+    key.timed = pe != nullptr;
+    return launch_cached(key, st, enqueue, pe, sink);
 }
 }  // namespace
 }  // namespace gee
@@ -465,30 +615,42 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
               const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
               size_t workspace_bytes, void *stream, uint32_t *d_status) {
     return embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes, stream,
-                      d_status, nullptr);
+                      d_status, nullptr, nullptr);
+}
+
+int gee_graph_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(gee::g_cache_mu);
+    if (!gee::g_cache) return GEE_OK;
+    int cur = 0;
+    const bool have_dev = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto &e : *gee::g_cache) {
+        if (e.exec && have_dev) cudaSetDevice(e.key.device);
+        gee::drop_entry(e);
+    }
+    if (have_dev) cudaSetDevice(cur);
+    gee::g_cache->clear();
+    return GEE_OK;
 }
 
 int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                     const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
                     size_t workspace_bytes, void *stream, uint32_t *d_status, float *phase_ms) {
     if (!phase_ms) return GEE_ERR_ARG;
+    for (int i = 0; i < kNumPhases; ++i) phase_ms[i] = -1.0f;
     PhaseEvents pe;
-    for (int i = 0; i <= kNumPhases; ++i)
-        if (cudaEventCreate(&pe.ev[i]) != cudaSuccess) {
-            for (int j = 0; j < i; ++j) cudaEventDestroy(pe.ev[j]);
-            return GEE_ERR_CUDA;
+    GEE_TRY(create_events(pe));
+    const PhaseSink sink = [&](const PhaseEvents &used) -> int {
+        GEE_TRY(cuda_check(cudaEventSynchronize(used.ev[kNumPhases])));
+        for (int i = 0; i < kNumPhases; ++i) {
+            float ms = -1.0f;
+            if (used.ran[i] && cudaEventElapsedTime(&ms, used.ev[i], used.ev[i + 1]) != cudaSuccess) ms = -1.0f;
+            phase_ms[i] = ms;
         }
-    int rc = embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes, stream,
-                        d_status, &pe);
-    if (rc == GEE_OK && cudaEventSynchronize(pe.ev[kNumPhases]) != cudaSuccess) rc = GEE_ERR_CUDA;
-    for (int i = 0; i < kNumPhases; ++i) {
-        float ms = -1.0f;
-        if (rc == GEE_OK && pe.ran[i]) {
-            if (cudaEventElapsedTime(&ms, pe.ev[i], pe.ev[i + 1]) != cudaSuccess) ms = -1.0f;
-        }
-        phase_ms[i] = ms;
-    }
-    for (int i = 0; i <= kNumPhases; ++i) cudaEventDestroy(pe.ev[i]);
+        return GEE_OK;
+    };
+    const int rc = embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes,
+                              stream, d_status, &pe, &sink);
+    destroy_events(pe);
     return rc;
 }
 
