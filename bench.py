@@ -81,8 +81,8 @@ def kernel_bytes(g):
     else:
         b["k_scatter_final"] = E * (8 + 4 * wt) + E * (4 + 4 * wt)   # read src/dst/w, write col/val
     b["k_rowscan"] = 4 * N + 4 * (N + 1) + (0 if wt else 4 * N + 16 * N)
-    b["k_wdeg_rows"] = 4 * E + 4 * (N + 1) + 4 * N + 16 * N if wt else 0
-    b["k_spmm_rows"] = E * (4 + 4 * wt) + 4 * (N + 1) + 8 * N + 4 * N + 4 * N * K
+    b["k_wdeg"] = 4 * E + 4 * (N + 1) + 4 * N + 16 * N if wt else 0
+    b["k_spmm"] = E * (4 + 4 * wt) + 4 * (N + 1) + 8 * N + 4 * N + 4 * N * K
     return b
 
 

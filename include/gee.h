@@ -140,10 +140,11 @@ int gee_graph_cache_clear(void);
  *   range), 2 k_offsets (first pass), 3 k_scatter first pass (graphs with more than
  *   2^11 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final
  *   pass), 6 k_scatter final pass (writes the CSR), 7 k_rowscan (index_pointers,
- *   unweighted degrees), 8 k_hubprep (hub-row chunks), 9 k_wdeg_hub and 10 k_wdeg_rows
- *   (weighted degrees), 11 k_spmm_hub and 12 k_spmm_rows (Z with the fused epilogue).
+ *   unweighted degrees, hub-row list and chunks), 8 k_wdeg (weighted degrees, hub
+ *   chunks then light rows), 9 k_spmm (Z with the fused epilogue, hub chunks then
+ *   light rows).
  */
-#define GEE_NUM_PHASES 13
+#define GEE_NUM_PHASES 10
 int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                     const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
                     void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status,

@@ -58,7 +58,7 @@ PENDING = 7
 ERR_STATE = 8
 
 PHASES = ("memset", "k_prep", "k_offsets_first", "k_scatter_first", "k_count", "k_offsets_final",
-          "k_scatter_final", "k_rowscan", "k_hubprep", "k_wdeg_hub", "k_wdeg_rows", "k_spmm_hub", "k_spmm_rows")
+          "k_scatter_final", "k_rowscan", "k_wdeg", "k_spmm")
 
 MAX_N = 1 << 21
 MAX_E = 1 << 30

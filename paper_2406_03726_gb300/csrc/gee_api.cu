@@ -2,8 +2,9 @@
 //
 // A call is planned on the host (digit widths, split threshold, lanes per row, the
 // workspace layout) and then enqueued on the caller's stream as: one memset of the
-// zero-initialised part of the workspace, then k_prep, k_sort (1 or 2 passes),
-// k_rowscan, k_hubprep, k_wdeg (weighted Laplacian only) and k_spmm.  Nothing is
+// zero-initialised part of the workspace, then k_prep, k_offsets and k_scatter (1 or 2
+// radix passes, with k_count between them), k_rowscan, k_wdeg (weighted Laplacian only)
+// and k_spmm.  Nothing is
 // allocated and nothing synchronises, so the sequence can be captured in a CUDA graph.
 #include "gee_internal.cuh"
 #include "../../include/gee.h"
@@ -25,18 +26,14 @@ cudaError_t launch_scatter(const Ctx &c, int blocks, bool final_pass, int max_di
 size_t scatter_smem(int max_digit_bits);
 cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st);
-cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st);
-cudaError_t launch_wdeg(const Ctx &c, int hub_blocks, int row_blocks, cudaStream_t st);
-cudaError_t launch_spmm_hub(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
-cudaError_t launch_spmm_rows(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
+cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st);
+cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
 cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32_t N, const int32_t *y, int32_t K,
                                 int32_t *C, int blocks, cudaStream_t st);
 cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st);
 cudaError_t configure_kernels();
-int occupancy_spmm_rows(bool smem_acc);
-int occupancy_spmm_hub(bool smem_acc);
-int occupancy_wdeg_rows();
-int occupancy_wdeg_hub();
+int occupancy_spmm(bool smem_acc);
+int occupancy_wdeg();
 
 namespace {
 
@@ -47,9 +44,8 @@ constexpr size_t kSmemPerSM = 228 * 1024;   // shared memory per SM usable by CT
 struct DeviceInfo {
     bool ready = false;
     int sms = 0;
-    int occ_rows[2] = {1, 1};  // k_spmm_rows without / with shared-memory accumulators
-    int occ_hub[2] = {1, 1};   // k_spmm_hub
-    int occ_wrows = 1, occ_whub = 1;
+    int occ_spmm[2] = {1, 1};  // CTAs per SM of k_spmm without / with shared-memory accumulators
+    int occ_wdeg = 1;
 };
 
 std::mutex g_mu;
@@ -63,12 +59,8 @@ int device_info(DeviceInfo &out) {
     if (!d.ready) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEE_ERR_CUDA;
         if (configure_kernels() != cudaSuccess) return GEE_ERR_CUDA;
-        for (int i = 0; i < 2; ++i) {
-            d.occ_rows[i] = occupancy_spmm_rows(i == 1);
-            d.occ_hub[i] = occupancy_spmm_hub(i == 1);
-        }
-        d.occ_wrows = occupancy_wdeg_rows();
-        d.occ_whub = occupancy_wdeg_hub();
+        for (int i = 0; i < 2; ++i) d.occ_spmm[i] = occupancy_spmm(i == 1);
+        d.occ_wdeg = occupancy_wdeg();
         d.ready = true;
     }
     out = d;
@@ -157,9 +149,8 @@ uint32_t chunk_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / d.hub_C) + h
 void layout_zero(Bump &b, GraphDesc &d) {
     d.rowcnt = b.take<int32_t>((size_t)d.N);
     d.nk = b.take<int32_t>((size_t)d.K);
-    d.hist1 = b.take<uint32_t>((size_t)1 << first_bits(d));
-    d.hist2 = d.npass == 2 ? b.take<uint32_t>((size_t)1 << d.fbits) : nullptr;
-    d.lb_s = b.take<uint32_t>((size_t)d.tiles_n);
+    d.hist1 = b.take<uint32_t>((size_t)kHistCopies << first_bits(d));
+    d.hist2 = d.npass == 2 ? b.take<uint32_t>((size_t)kHistCopies << d.fbits) : nullptr;
 }
 
 void layout_rest(Bump &b, GraphDesc &d, bool weighted) {
@@ -264,10 +255,7 @@ enum Phase {
     kPhOffs2,
     kPhScatF,
     kPhRowscan,
-    kPhHubprep,
-    kPhWdegHub,
     kPhWdeg,
-    kPhSpmmHub,
     kPhSpmm,
     kNumPhases
 };
@@ -331,21 +319,20 @@ int run_plan(const LaunchPlan &lp, const DeviceInfo &dev, cudaStream_t st, Phase
     GEE_PHASE(kPhOffs2, lp.items[kPfxOffs2] > 0, launch_offsets(ctx(kPfxOffs2), lp.items[kPfxOffs2], true, st));
     GEE_PHASE(kPhScatF, lp.items[kPfxScatF] > 0, launch_scatter(ctx(kPfxScatF), lp.items[kPfxScatF], true, lp.fmax, st));
     GEE_PHASE(kPhRowscan, lp.items[kPfxScan] > 0, launch_rowscan(ctx(kPfxScan), lp.items[kPfxScan], st));
-    const bool hubs = cb.hub_cap > 0 && (embed || lp.any_wdeg);
-    GEE_PHASE(kPhHubprep, hubs, launch_hubprep(cb, st));
+    // k_wdeg and k_spmm take the hub chunks first (CTA by CTA), then the light rows (warp
+    // by warp): grids cover whichever part has more parallel work, within one wave
     const int64_t hub_grid_max = cb.hub_cap > 0 ? cb.chunk_cap : 0;
-    // hub kernels: a grid of at most one CTA per SM (they leave at once when no row is split)
-    const int whub = (int)std::min<int64_t>(lp.any_wdeg ? hub_grid_max : 0, (int64_t)dev.sms);
     const int64_t wrow_items = lp.items[kPfxWRows];
-    const int wrows = (int)std::min<int64_t>((wrow_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_wrows);
-    GEE_PHASE(kPhWdegHub, whub > 0, launch_wdeg(ctx(kPfxWRows), whub, 0, st));
-    GEE_PHASE(kPhWdeg, wrows > 0, launch_wdeg(ctx(kPfxWRows), 0, wrows, st));
+    const int64_t wneed = std::max<int64_t>(lp.any_wdeg ? std::min<int64_t>(hub_grid_max, dev.sms) : 0,
+                                            (wrow_items + kWarps - 1) / kWarps);
+    const int wgrid = (int)std::min<int64_t>(wneed, (int64_t)dev.sms * dev.occ_wdeg);
+    GEE_PHASE(kPhWdeg, lp.any_wdeg && wgrid > 0, launch_wdeg(ctx(kPfxWRows), wgrid, st));
     const int sm = lp.smem_acc ? 1 : 0;
-    const int shub = (int)std::min<int64_t>(hub_grid_max, (int64_t)dev.sms * std::min(2, dev.occ_hub[sm]));
     const int64_t row_items = lp.items[kPfxRows];
-    const int srows = (int)std::min<int64_t>((row_items + kWarps - 1) / kWarps, (int64_t)dev.sms * dev.occ_rows[sm]);
-    GEE_PHASE(kPhSpmmHub, embed && shub > 0, launch_spmm_hub(ctx(kPfxRows), shub, lp.smem_acc, st));
-    GEE_PHASE(kPhSpmm, embed && srows > 0, launch_spmm_rows(ctx(kPfxRows), srows, lp.smem_acc, st));
+    const int64_t sneed = std::max<int64_t>(std::min<int64_t>(hub_grid_max, 2 * (int64_t)dev.sms),
+                                            (row_items + kWarps - 1) / kWarps);
+    const int sgrid = (int)std::min<int64_t>(sneed, (int64_t)dev.sms * dev.occ_spmm[sm]);
+    GEE_PHASE(kPhSpmm, embed && sgrid > 0, launch_spmm(ctx(kPfxRows), sgrid, lp.smem_acc, st));
     GEE_TRY(mark(pe, kNumPhases, st));
     return GEE_OK;
 }

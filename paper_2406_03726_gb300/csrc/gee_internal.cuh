@@ -18,19 +18,15 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kSortItems = 8;                  // keys per thread in a sort pass
 constexpr int kSortTile = kThreads * kSortItems;   // 2048 edges per sort tile
 constexpr int kPrepTile = 8192;                // edges (or nodes) per histogram tile
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kThreads * kScanItems;   // 4096 nodes per scan tile
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;   // 2048 nodes per index-pointer tile
 constexpr int kMaxDigitBits = 11;
 constexpr int kMaxDigits = 1 << kMaxDigitBits;     // 2048 buckets per radix pass
 constexpr int kMaxK = 64;
 constexpr int kRegK = 8;                       // K <= 8: per-lane register accumulators
+constexpr int kHistCopies = 8;                 // digit totals are spread over 8 copies: fewer
+                                               // atomics on one address at the end of k_prep
 
-// ---- look-back status words (one 32-bit word per tile x bucket) -------------------------
-// bits 31..30: 0 = nothing published, 1 = tile aggregate, 2 = inclusive prefix
-// bits 29..0 : the count (edge counts are < 2^30)
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagPre = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;            // bounded waits: ~1 s, then GEE_STATUS_TIMEOUT
 
 // status bits (must equal GEE_STATUS_* in gee.h)
@@ -66,11 +62,10 @@ struct GraphDesc {
     float *val;              // [E + 4]       weighted only
     uint32_t *tmpk;          // [E]           2-pass: (src >> lbits) << nbits | dst
     float *tmpw;             // [E]           2-pass weighted
-    uint32_t *hist1;         // [2^b1]        zeroed: first-pass digit totals (b1 = lbits, or fbits for 1 pass)
-    uint32_t *hist2;         // [2^fbits]     zeroed: final-pass digit totals (2-pass graphs)
+    uint32_t *hist1;         // [kHistCopies][2^b1] zeroed: first-pass digit totals (b1 = lbits, or fbits for 1 pass)
+    uint32_t *hist2;         // [kHistCopies][2^fbits] zeroed: final-pass digit totals (2-pass graphs)
     uint32_t *cnt1;          // [ranges << b1]    per-range first-pass digit counts, then bucket offsets
     uint32_t *cnt2;          // [ranges << fbits] per-range final-pass digit counts, then offsets (2-pass)
-    uint32_t *lb_s;          // [tiles_n]     zeroed
     int32_t *nk;             // [K]           zeroed
     float *deg;              // [N]  D_ii
     float *dinv;             // [N]  D_ii^-1/2 (1 without the Laplacian)

@@ -8,9 +8,9 @@
 //              data)
 //   k_count    (graphs with more than 2^11 nodes) final-digit histograms of the packed
 //              first-pass output and the row lengths
-//   k_rowscan  index_pointers by a look-back scan of the row lengths; unweighted degrees
-//              D_ii and the node table s_j = D_jj^-1/2 / n_{y_j}; hub-row list
-//   k_hubprep  chunk offsets of the split (hub) rows
+//   k_rowscan  index_pointers from the last pass's bucket offsets and the row lengths;
+//              unweighted degrees D_ii and the node table s_j = D_jj^-1/2 / n_{y_j};
+//              hub-row list and (last CTA) the chunk offsets of the split rows
 //   k_wdeg     weighted degrees: FP32 compensated sums on light rows, FP64 chunk
 //              partials merged in FP64 on hub rows; then D^-1/2 and the node table
 //   k_spmm     Z = D^-1/2 (A + I) D^-1/2 W as a label-gather over the CSR rows, with the
@@ -38,16 +38,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // streaming loads of data read exactly once (no L1 allocation)
@@ -150,201 +140,6 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
 // ------------------------------------------------------------------------------------
-// k_prep: histograms of source-id digits (edge tiles), class sizes n_k (node tiles)
-
-// ------------------------------------------------------------------------------------
-// CSR build: stable LSD radix sort of the edges by source id (Section 3 CSR, rows in
-// input order).  A graph's edges are cut into ranges of range_tiles x 4096 edges.
-//
-//   k_prep       per range: histogram of the first-pass digit of the source ids
-//                (low lbits for 2-pass graphs, the whole id for graphs with <= 2^11
-//                nodes); per node tile: class sizes n_k and label checks
-//   k_offsets    per digit: exclusive prefix over (digit, range) -> the bucket offset
-//                at which each range starts writing each digit
-//   k_scatter    one CTA per range scatters its tiles in order from those offsets:
-//                first pass -> packed ((src >> lbits) << nbits | dst) + weight,
-//                final pass -> col / val of the CSR
-//   k_count      (2-pass graphs) per range of the packed array: histogram of the
-//                final-pass digit, and the exact row lengths rowcnt
-// No CTA ever waits for another: the offsets are known before a range is scattered.
-
-constexpr int kPrivDigits = 512;  // digit counts up to this get one private histogram per warp
-
-__device__ __forceinline__ int64_t range_begin(const GraphDesc &g, int r) {
-    return (int64_t)r * g.range_tiles * kSortTile;
-}
-__device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
-    return (int)min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
-}
-
-// Stream the ids [0, n) of p through f(value): a scalar head up to the first 16-byte
-// boundary, then 16-byte vectors (8 per thread in flight), then a scalar tail.
-template <class F>
-__device__ __forceinline__ void stream_ids(const int32_t *p, int n, F &&f) {
-    int head = (int)(((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) >> 2);
-    if ((reinterpret_cast<uintptr_t>(p) & 3u) != 0) head = n;  // not even 4-byte aligned: scalar
-    head = min(head, n);
-    if ((int)threadIdx.x < head) f(ld_stream(p + threadIdx.x));
-    p += head;
-    n -= head;
-    constexpr int kV = 8;
-    const int nv = n >> 2;
-    for (int base = 0; base < nv; base += kV * kThreads) {
-        int4 v[kV];
-#pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            const int vi = base + threadIdx.x + k * kThreads;
-            v[k] = vi < nv ? ld_stream4(p + 4 * vi) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            if (base + (int)threadIdx.x + k * kThreads < nv) {
-                f(v[k].x);
-                f(v[k].y);
-                f(v[k].z);
-                f(v[k].w);
-            }
-        }
-    }
-    if ((int)threadIdx.x < n - 4 * nv) f(ld_stream(p + 4 * nv + threadIdx.x));
-}
-
-__global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
-    __shared__ GraphDesc sg;
-    __shared__ int sl[2];
-    __shared__ uint32_t h[kWarps * kPrivDigits];
-    __shared__ uint32_t s_err;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
-    if (tid == 0) s_err = 0;
-    uint32_t err = 0;
-    if (t < sg.ranges) {
-        const int b1 = first_bits(sg);
-        const int D = 1 << b1;
-        const int str = (D <= kPrivDigits) ? D : 0;  // private per-warp histograms when they fit
-        const int nh = str ? kWarps * D : D;
-        for (int i = tid; i < nh; i += kThreads) h[i] = 0;
-        __syncthreads();
-        uint32_t *hw = h + warp * str;
-        const uint32_t N = (uint32_t)sg.N;
-        const uint32_t m = (1u << b1) - 1u;
-        stream_ids(sg.src + range_begin(sg, t), range_len(sg, t), [&](int v) {
-            if ((uint32_t)v >= N) {
-                err |= kStIndex;
-                v = 0;
-            }
-            atomicAdd(&hw[(uint32_t)v & m], 1u);
-        });
-        __syncthreads();
-        uint32_t *out = sg.cnt1 + ((size_t)t << b1);
-        for (int d = tid; d < D; d += kThreads) {
-            uint32_t v = 0;
-            if (str)
-                for (int w = 0; w < kWarps; ++w) v += h[w * D + d];
-            else
-                v = h[d];
-            out[d] = v;
-            if (v) atomicAdd(&sg.hist1[d], v);
-        }
-    } else {
-        const int64_t n0 = (int64_t)(t - sg.ranges) * kPrepTile;
-        const int n = (int)min64(kPrepTile, (int64_t)sg.N - n0);
-        const int K = sg.K;
-        for (int i = tid; i < K; i += kThreads) h[i] = 0;
-        __syncthreads();
-        for (int i = tid; i < n; i += kThreads) {
-            int yv = __ldg(sg.y + n0 + i);
-            if (yv < -1 || yv >= K) err |= kStLabel;
-            else if (yv >= 0) atomicAdd(&h[yv], 1u);
-        }
-        __syncthreads();
-        for (int i = tid; i < K; i += kThreads)
-            if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h[i]);
-    }
-    if (err) atomicOr(&s_err, err);
-    __syncthreads();
-    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
-}
-
-// k_offsets: for a block of 32 digits, rewrite cnt[r][d] (counts) as the position where
-// range r writes its first element of digit d: dbase[d] + sum_{r' < r} cnt[r'][d], with
-// dbase the exclusive prefix over digits of the totals.  1024 threads: lane = digit of
-// the block, each of the 32 warps owns a slice of the ranges (8 loads in flight).
-constexpr int kOffThreads = 1024;
-constexpr int kOffWarps = kOffThreads / 32;
-
-template <bool SECOND>
-__global__ void __launch_bounds__(kOffThreads) k_offsets(Ctx c) {
-    __shared__ GraphDesc sg;
-    __shared__ int sl[2];
-    __shared__ uint32_t s_red[kOffWarps];
-    __shared__ uint32_t csum[kOffWarps][33];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int b = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
-    const int bits = SECOND ? sg.fbits : first_bits(sg);
-    const int D = 1 << bits;
-    uint32_t *cnt = SECOND ? sg.cnt2 : sg.cnt1;
-    const uint32_t *tot = SECOND ? sg.hist2 : sg.hist1;
-    const int d0 = 32 * b, d = d0 + lane;
-    // sum of the totals below this digit block
-    uint32_t part = 0;
-    for (int i = tid; i < d0; i += kOffThreads) part += __ldcg(tot + i);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) s_red[warp] = part;
-    __syncthreads();
-    uint32_t below = 0;
-    for (int w = 0; w < kOffWarps; ++w) below += s_red[w];
-    const uint32_t td = d < D ? __ldcg(tot + d) : 0u;
-    uint32_t x = td;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    const uint32_t dbase = below + x - td;
-    const int R = sg.ranges;
-    const int chunk = (R + kOffWarps - 1) / kOffWarps;
-    const int r0 = min(R, warp * chunk), r1 = min(R, r0 + chunk);
-    uint32_t s = 0;
-    if (d < D) {
-        int r = r0;
-        for (; r + 8 <= r1; r += 8) {
-            uint32_t a[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) s += a[q];
-        }
-        for (; r < r1; ++r) s += __ldcg(cnt + ((size_t)r << bits) + d);
-    }
-    csum[warp][lane] = s;
-    __syncthreads();
-    uint32_t run = dbase;
-    for (int w = 0; w < warp; ++w) run += csum[w][lane];
-    if (d < D) {
-        int r = r0;
-        for (; r + 8 <= r1; r += 8) {
-            uint32_t a[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                cnt[((size_t)(r + q) << bits) + d] = run;
-                run += a[q];
-            }
-        }
-        for (; r < r1; ++r) {
-            uint32_t *p = cnt + ((size_t)r << bits) + d;
-            const uint32_t v = __ldcg(p);
-            *p = run;
-            run += v;
-        }
-        if (!SECOND && sg.npass == 1 && warp == 0 && d < sg.N) sg.rowcnt[d] = (int32_t)td;  // digit = row
-    }
-}
-
-// ------------------------------------------------------------------------------------
 // TMA bulk copies (global -> shared memory, completion counted on an mbarrier)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -390,37 +185,262 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Windowed decoupled look-back: the predecessors' statuses are read 8 at a time, so a
-// chain of aggregates costs one round trip per 8 tiles.
-__device__ __forceinline__ uint32_t look_back8(const uint32_t *lb, int width, int t, int d, uint32_t &err) {
-    uint32_t excl = 0;
-    int j = t - 1, spins = 0;
-    while (j >= 0) {
-        uint32_t v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = (j - q >= 0) ? ld_relaxed(lb + (size_t)(j - q) * width + d) : kFlagPre;
-        int q = 0;
-        bool done = false;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            if (done || q != r) continue;
-            const uint32_t f = v[r] & ~kValMask;
-            if (f == 0u) continue;  // not published yet: stop here, q stays r
-            excl += v[r] & kValMask;
-            if (f == kFlagPre) done = true;
-            q = r + 1;
+// ------------------------------------------------------------------------------------
+// k_prep: histograms of source-id digits (edge tiles), class sizes n_k (node tiles)
+
+// ------------------------------------------------------------------------------------
+// CSR build: stable LSD radix sort of the edges by source id (Section 3 CSR, rows in
+// input order).  A graph's edges are cut into ranges of range_tiles x 4096 edges.
+//
+//   k_prep       per range: histogram of the first-pass digit of the source ids
+//                (low lbits for 2-pass graphs, the whole id for graphs with <= 2^11
+//                nodes); per node tile: class sizes n_k and label checks
+//   k_offsets    per digit: exclusive prefix over (digit, range) -> the bucket offset
+//                at which each range starts writing each digit
+//   k_scatter    one CTA per range scatters its tiles in order from those offsets:
+//                first pass -> packed ((src >> lbits) << nbits | dst) + weight,
+//                final pass -> col / val of the CSR
+//   k_count      (2-pass graphs) per range of the packed array: histogram of the
+//                final-pass digit, and the exact row lengths rowcnt
+// No CTA ever waits for another: the offsets are known before a range is scattered.
+
+constexpr int kPrivDigits = 512;  // digit counts up to this get one private histogram per warp
+
+__device__ __forceinline__ int64_t range_begin(const GraphDesc &g, int r) {
+    return (int64_t)r * g.range_tiles * kSortTile;
+}
+__device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
+    return (int)min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
+}
+
+// Stream the ids [0, n) of p through f(value), CTA-wide, through shared memory: stages of
+// 2048 ids are filled by TMA bulk copies, kIdStages of them in flight, and each thread
+// then takes 8 ids of a stage as two 16-byte reads.  The head up to the first 16-byte
+// boundary and the last n mod 4 ids are read directly.  Every thread of the CTA calls it
+// with the same arguments; `parity` (one bit per stage barrier) is kept by the caller.
+constexpr int kIdStages = 4;
+constexpr int kIdStage = 2048;
+constexpr size_t kIdRingBytes = (size_t)kIdStages * kIdStage * 4;
+
+struct IdRing {
+    int32_t *buf;   // [kIdStages][kIdStage], dynamic shared memory
+    uint64_t *bar;  // [kIdStages] mbarriers, initialised with count 1
+};
+
+__device__ __forceinline__ void id_ring_init(const IdRing &ring) {
+    if (threadIdx.x == 0)
+        for (int s = 0; s < kIdStages; ++s) mbar_init(&ring.bar[s], 1);
+}
+
+template <class F>
+__device__ __forceinline__ void stream_ids_staged(const int32_t *p, int n, const IdRing &ring, uint32_t &parity,
+                                                  uint32_t &err, F &&f) {
+    const int tid = threadIdx.x;
+    int head = (int)(((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) >> 2);
+    if ((reinterpret_cast<uintptr_t>(p) & 3u) != 0) head = n;  // not even 4-byte aligned: all direct
+    head = min(head, n);
+    if (tid < head) f(ld_stream(p + tid));
+    p += head;
+    n -= head;
+    const int nb = n & ~3;
+    const int nst = (nb + kIdStage - 1) / kIdStage;
+    auto issue = [&](int s) {
+        const int slot = s % kIdStages;
+        const uint32_t bytes = (uint32_t)min(kIdStage, nb - s * kIdStage) * 4u;
+        mbar_expect_tx(&ring.bar[slot], bytes);
+        bulk_g2s(ring.buf + slot * kIdStage, p + (size_t)s * kIdStage, bytes, &ring.bar[slot]);
+    };
+    __syncthreads();  // earlier reads of the ring are done
+    if (tid == 0 && nst > 0) {
+        fence_proxy_async();
+        for (int s = 0; s < min(kIdStages, nst); ++s) issue(s);
+    }
+    for (int s = 0; s < nst; ++s) {
+        const int slot = s % kIdStages;
+        const int cnt4 = min(kIdStage, nb - s * kIdStage) >> 2;
+        if (!mbar_wait(&ring.bar[slot], (parity >> slot) & 1u)) err |= kStTimeout;
+        parity ^= 1u << slot;
+        const int4 *v = reinterpret_cast<const int4 *>(ring.buf + slot * kIdStage);
+        for (int i = tid; i < cnt4; i += kThreads) {
+            const int4 x = v[i];
+            f(x.x);
+            f(x.y);
+            f(x.z);
+            f(x.w);
         }
-        if (done) break;
-        j -= q;
-        if (q == 0) {
-            if (++spins > kSpinLimit) {
-                err |= kStTimeout;
-                break;
-            }
-            if (spins > 16) __nanosleep(64);
+        __syncthreads();  // the stage is consumed
+        if (tid == 0 && s + kIdStages < nst) {
+            fence_proxy_async();
+            issue(s + kIdStages);
         }
     }
-    return excl;
+    if (tid < n - nb) f(ld_stream(p + nb + tid));
+}
+
+__global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ uint32_t h[kWarps * kPrivDigits];
+    __shared__ uint32_t s_err;
+    __shared__ __align__(8) uint64_t bars[kIdStages];
+    extern __shared__ __align__(128) int32_t ringbuf[];
+    const IdRing ring{ringbuf, bars};
+    const int tid = threadIdx.x, warp = tid >> 5;
+    id_ring_init(ring);
+    const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    if (tid == 0) s_err = 0;
+    uint32_t err = 0;
+    if (t < sg.ranges) {
+        const int b1 = first_bits(sg);
+        const int D = 1 << b1;
+        const int str = (D <= kPrivDigits) ? D : 0;  // private per-warp histograms when they fit
+        const int nh = str ? kWarps * D : D;
+        for (int i = tid; i < nh; i += kThreads) h[i] = 0;
+        __syncthreads();
+        uint32_t *hw = h + warp * str;
+        const uint32_t N = (uint32_t)sg.N;
+        const uint32_t m = (1u << b1) - 1u;
+        uint32_t parity = 0;
+        stream_ids_staged(sg.src + range_begin(sg, t), range_len(sg, t), ring, parity, err, [&](int v) {
+            if ((uint32_t)v >= N) {
+                err |= kStIndex;
+                v = 0;
+            }
+            atomicAdd(&hw[(uint32_t)v & m], 1u);
+        });
+        __syncthreads();
+        uint32_t *out = sg.cnt1 + ((size_t)t << b1);
+        for (int d = tid; d < D; d += kThreads) {
+            uint32_t v = 0;
+            if (str)
+                for (int w = 0; w < kWarps; ++w) v += h[w * D + d];
+            else
+                v = h[d];
+            out[d] = v;
+            if (v) atomicAdd(&sg.hist1[((size_t)(t % kHistCopies) << b1) + d], v);
+        }
+    } else {
+        const int64_t n0 = (int64_t)(t - sg.ranges) * kPrepTile;
+        const int n = (int)min64(kPrepTile, (int64_t)sg.N - n0);
+        const int K = sg.K;
+        for (int i = tid; i < K; i += kThreads) h[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += kThreads) {
+            int yv = __ldg(sg.y + n0 + i);
+            if (yv < -1 || yv >= K) err |= kStLabel;
+            else if (yv >= 0) atomicAdd(&h[yv], 1u);
+        }
+        __syncthreads();
+        for (int i = tid; i < K; i += kThreads)
+            if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h[i]);
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(sg.status, s_err);
+}
+
+// k_offsets: for a block of 32 digits, rewrite cnt[r][d] (counts) as the position where
+// range r writes its first element of digit d: dbase[d] + sum_{r' < r} cnt[r'][d], with
+// dbase the exclusive prefix over digits of the totals.  1024 threads: lane = digit of
+// the block, each of the 32 warps owns a slice of the ranges (8 loads in flight).
+constexpr int kOffThreads = 1024;
+constexpr int kOffWarps = kOffThreads / 32;
+
+template <bool SECOND>
+__global__ void __launch_bounds__(kOffThreads) k_offsets(Ctx c) {
+    __shared__ GraphDesc sg;
+    __shared__ int sl[2];
+    __shared__ uint32_t s_red[kOffWarps];
+    __shared__ uint32_t csum[kOffWarps][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
+    const int bits = SECOND ? sg.fbits : first_bits(sg);
+    const int D = 1 << bits;
+    uint32_t *cnt = SECOND ? sg.cnt2 : sg.cnt1;
+    const uint32_t *tot = SECOND ? sg.hist2 : sg.hist1;
+    const int d0 = 32 * b, d = d0 + lane;
+    const int R = sg.ranges;
+    const int chunk = (R + kOffWarps - 1) / kOffWarps;
+    const int r0 = min(R, warp * chunk), r1 = min(R, r0 + chunk);
+    // this warp's counts, kept in registers between the two passes when they fit
+    constexpr int kHold = 24;
+    const bool hold = chunk <= kHold;
+    uint32_t held[kHold];
+    uint32_t s = 0;
+    if (hold && d < D) {
+#pragma unroll
+        for (int q = 0; q < kHold; ++q) held[q] = (r0 + q < r1) ? __ldcg(cnt + ((size_t)(r0 + q) << bits) + d) : 0u;
+    }
+    // sum of the totals below this digit block
+    uint32_t part = 0;
+    for (int i = tid; i < d0 * kHistCopies; i += kOffThreads) {
+        const int cpy = i / d0, dd = i - cpy * d0;
+        part += __ldcg(tot + ((size_t)cpy << bits) + dd);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_red[warp] = part;
+    uint32_t td = 0;
+    if (d < D)
+#pragma unroll
+        for (int cpy = 0; cpy < kHistCopies; ++cpy) td += __ldcg(tot + ((size_t)cpy << bits) + d);
+    if (d < D) {
+        if (hold) {
+#pragma unroll
+            for (int q = 0; q < kHold; ++q) s += held[q];
+        } else {
+            int r = r0;
+            for (; r + 8 <= r1; r += 8) {
+                uint32_t a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s += a[q];
+            }
+            for (; r < r1; ++r) s += __ldcg(cnt + ((size_t)r << bits) + d);
+        }
+    }
+    csum[warp][lane] = s;
+    __syncthreads();
+    uint32_t below = 0;
+    for (int w = 0; w < kOffWarps; ++w) below += s_red[w];
+    uint32_t x = td;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t run = below + x - td;  // bucket base of digit d
+    for (int w = 0; w < warp; ++w) run += csum[w][lane];
+    if (d < D) {
+        if (hold) {
+#pragma unroll
+            for (int q = 0; q < kHold; ++q)
+                if (r0 + q < r1) {
+                    cnt[((size_t)(r0 + q) << bits) + d] = run;
+                    run += held[q];
+                }
+        } else {
+            int r = r0;
+            for (; r + 8 <= r1; r += 8) {
+                uint32_t a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] = __ldcg(cnt + ((size_t)(r + q) << bits) + d);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    cnt[((size_t)(r + q) << bits) + d] = run;
+                    run += a[q];
+                }
+            }
+            for (; r < r1; ++r) {
+                uint32_t *p = cnt + ((size_t)r << bits) + d;
+                const uint32_t v = __ldcg(p);
+                *p = run;
+                run += v;
+            }
+        }
+        if (!SECOND && sg.npass == 1 && warp == 0 && d < sg.N) sg.rowcnt[d] = (int32_t)td;  // digit = row
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -750,7 +770,11 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
     __shared__ uint32_t seg[kMaxDigits];
     __shared__ int s_lo[2];
     __shared__ uint32_t s_err;
+    __shared__ __align__(8) uint64_t bars[kIdStages];
+    extern __shared__ __align__(128) int32_t ringbuf[];
+    const IdRing ring{ringbuf, bars};
     const int tid = threadIdx.x;
+    id_ring_init(ring);
     const int r = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     const int D2 = 1 << sg.fbits, D1 = 1 << sg.lbits;
     const int nb = sg.nbits, lb = sg.lbits;
@@ -778,13 +802,15 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
         const int str = (D2 * kWarps <= kMaxDigits) ? D2 : 0;  // private per-warp histograms
         const int nseg = str ? kWarps * D2 : D2;
         uint32_t *hw = seg + warp * str;
+        uint32_t parity = 0;
         for (int l = lof; l <= lol; ++l) {
             const int64_t ps = max((int64_t)__ldcg(lobase + l), e0);
             const int64_t pe = min(l + 1 < D1 ? (int64_t)__ldcg(lobase + l + 1) : sg.E, e0 + n);
             if (pe <= ps) continue;
             for (int d = tid; d < nseg; d += kThreads) seg[d] = 0;
             __syncthreads();
-            stream_ids(reinterpret_cast<const int32_t *>(sg.tmpk + ps), (int)(pe - ps), [&](int v) {
+            stream_ids_staged(reinterpret_cast<const int32_t *>(sg.tmpk + ps), (int)(pe - ps), ring, parity, err,
+                              [&](int v) {
                 uint32_t hi = (uint32_t)v >> nb;
                 if (hi >= (uint32_t)D2) {
                     err |= kStTimeout;
@@ -831,7 +857,7 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
     for (int d = tid; d < D2; d += kThreads) {
         const uint32_t v = acc[d];
         out[d] = v;
-        if (v) atomicAdd(&sg.hist2[d], v);
+        if (v) atomicAdd(&sg.hist2[((size_t)(r % kHistCopies) << sg.fbits) + d], v);
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();
@@ -841,14 +867,14 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
 // ------------------------------------------------------------------------------------
 // node-table helpers
 
-// s_j = D_jj^-1/2 / n_{y_j} (Laplacian) or 1 / n_{y_j}; unlabelled nodes get {0, 0}
-__device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float deg, bool lap) {
+// s_j = D_jj^-1/2 / n_{y_j} (Laplacian) or 1 / n_{y_j}; unlabelled nodes get {0, 0}.
+// yv = y_j, ny = n_{y_j} (read by the caller when y_j is a class).
+__device__ __forceinline__ void write_node_known(const GraphDesc &g, int64_t j, float deg, bool lap, int yv,
+                                                 int ny) {
     const float dv = lap ? (deg > 0.0f ? 1.0f / sqrtf(deg) : 0.0f) : 1.0f;
-    int yv = __ldg(g.y + j);
     int2 tv = make_int2(0, 0);
     if (yv >= 0 && yv < g.K) {
-        const int cnt = __ldcg(g.nk + yv);
-        const float s = cnt > 0 ? dv / (float)cnt : 0.0f;
+        const float s = ny > 0 ? dv / (float)ny : 0.0f;
         tv = make_int2(yv, __float_as_int(s));
     }
     g.deg[j] = deg;
@@ -856,25 +882,51 @@ __device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float 
     g.tab[j] = tv;
 }
 
+__device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float deg, bool lap) {
+    const int yv = __ldg(g.y + j);
+    const int ny = (yv >= 0 && yv < g.K) ? __ldcg(g.nk + yv) : 0;
+    write_node_known(g, j, deg, lap, yv, ny);
+}
+
 // ------------------------------------------------------------------------------------
-// k_rowscan: rowptr = exclusive scan of rowcnt (look-back across 4096-node tiles)
+// k_rowscan: index pointers from the bucket offsets of the last radix pass.  The rows
+// of one final-pass digit hi are the 2^lbits consecutive ids (hi << lbits) | lo, in
+// order, so a row starts at the bucket base of hi (range 0's offset of digit hi) plus
+// the row lengths of the rows before it in that group.  1-pass graphs take the base
+// directly (there the digit is the row).  Tiles of 2048 rows hold whole groups, so no
+// tile depends on another.  Also: the hub list, and the node table when no weighted
+// degree is needed.
+
+// Chunk offsets of the hub rows (prefix over their chunk counts), by one CTA.
+__device__ void hub_chunk_offsets(const CallBufs &cb, uint32_t *s_scan) {
+    const uint32_t H = min(__ldcg(&cb.cs->hub_count), cb.hub_cap);
+    uint32_t base_run = 0;
+    for (uint32_t b = 0; b < H; b += kThreads) {
+        const uint32_t h = b + threadIdx.x;
+        const uint32_t v = h < H ? (uint32_t)__ldcg(&cb.hubs[h].nch) : 0u;
+        uint32_t tot;
+        const uint32_t x = block_excl_scan(v, s_scan, tot);
+        if (h < H) cb.chunk_off[h] = base_run + x;
+        base_run += tot;
+    }
+    if (threadIdx.x == 0) {
+        cb.chunk_off[H] = base_run;
+        cb.cs->hub_chunks = min(base_run, cb.chunk_cap);
+        cb.cs->hub_count = H;
+    }
+}
 
 __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
-    __shared__ int s_item;
     __shared__ uint32_t s_scan[kWarps];
-    __shared__ uint32_t s_excl;
     __shared__ int32_t buf[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_err;
+    __shared__ int s_last;
 
     const int tid = threadIdx.x;
-    if (tid == 0) {
-        s_item = (int)atomicAdd(&c.cb.cs->ctr[2], 1u);
-        s_err = 0;
-    }
-    __syncthreads();
-    const int t = load_desc(c, s_item, &sg, sl, c.prefix);
+    if (tid == 0) s_err = 0;
+    const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     const int64_t n0 = (int64_t)t * kScanTile;
     const int n = (int)min64(kScanTile, (int64_t)sg.N - n0);
     auto pad = [](int i) { return i + (i >> 5); };
@@ -885,18 +937,6 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     for (int j = 0; j < kScanItems; ++j) loc += (uint32_t)buf[pad(tid * kScanItems + j)];
     uint32_t tot;
     uint32_t run = block_excl_scan(loc, s_scan, tot);
-    uint32_t err = 0;
-    if (tid == 0) {
-        uint32_t ex = 0;
-        st_relaxed(sg.lb_s + t, (t == 0 ? kFlagPre : kFlagAgg) | tot);
-        if (t > 0) {
-            ex = look_back8(sg.lb_s, 1, t, 0, err);
-            st_relaxed(sg.lb_s + t, kFlagPre | ((ex + tot) & kValMask));
-        }
-        s_excl = ex;
-    }
-    __syncthreads();
-    run += s_excl;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int i = pad(tid * kScanItems + j);
@@ -905,13 +945,32 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
         run += cnt;
     }
     __syncthreads();
+    uint32_t err = 0;
+    const int sb = sg.npass == 2 ? sg.lbits : 0;
+    const int gmask = (1 << sb) - 1;  // row offset within its group
+    const uint32_t *bucket = sg.npass == 2 ? sg.cnt2 : sg.cnt1;
     const bool lap = (sg.flags & kOptLap) != 0;
     const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
-    for (int i = tid; i < n; i += kThreads) {
+    // every global read of the thread's rows first (one round trip each), then the writes
+    uint32_t base[kScanItems];
+    int yv[kScanItems], ny[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = tid + k * kThreads;
+        base[k] = (i < n && sg.E > 0) ? __ldcg(bucket + ((n0 + i) >> sb)) : 0u;
+        yv[k] = (i < n && !sg.wdeg) ? __ldg(sg.y + n0 + i) : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldcg(sg.nk + yv[k]) : 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = tid + k * kThreads;
+        if (i >= n) continue;
         const int64_t j = n0 + i;
-        const int32_t start = buf[pad(i)];
+        const uint32_t ex = (uint32_t)buf[pad(i)];
+        const int32_t cnt = (int32_t)((i + 1 < kScanTile ? (uint32_t)buf[pad(i + 1)] : tot) - ex);
+        const int32_t start = (int32_t)(base[k] + ex - (uint32_t)buf[pad(i & ~gmask)]);
         sg.rowptr[j] = start;
-        const int32_t cnt = __ldcg(sg.rowcnt + j);
         if (i == n - 1 && n0 + n == sg.N) sg.rowptr[sg.N] = start + cnt;
         if (cnt > sg.hub_C) {
             const uint32_t h = atomicAdd(&c.cb.cs->hub_count, 1u);
@@ -926,32 +985,19 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
                 err |= kStTimeout;  // capacity is sized so this cannot happen
             }
         }
-        if (!sg.wdeg) write_node(sg, j, (float)cnt + aug, lap);
+        if (!sg.wdeg) write_node_known(sg, j, (float)cnt + aug, lap, yv[k], ny[k]);
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (tid == 0 && s_err) atomicOr(sg.status, s_err);
-}
-
-// ------------------------------------------------------------------------------------
-// k_hubprep: chunk offsets of the hub rows (one CTA)
-
-__global__ void __launch_bounds__(kThreads) k_hubprep(CallBufs cb) {
-    __shared__ uint32_t s_scan[kWarps];
-    const uint32_t H = min(cb.cs->hub_count, cb.hub_cap);
-    uint32_t base_run = 0;
-    for (uint32_t b = 0; b < H; b += kThreads) {
-        const uint32_t h = b + threadIdx.x;
-        const uint32_t v = h < H ? (uint32_t)cb.hubs[h].nch : 0u;
-        uint32_t tot;
-        const uint32_t x = block_excl_scan(v, s_scan, tot);
-        if (h < H) cb.chunk_off[h] = base_run + x;
-        base_run += tot;
-    }
-    if (threadIdx.x == 0) {
-        cb.chunk_off[H] = base_run;
-        cb.cs->hub_chunks = min(base_run, cb.chunk_cap);
-        cb.cs->hub_count = H;
+    // the last CTA of the launch (over all graphs) turns the hub list into chunk offsets
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&c.cb.cs->ctr[2], 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        hub_chunk_offsets(c.cb, s_scan);
     }
 }
 
@@ -1090,17 +1136,22 @@ __device__ __forceinline__ void for_sorted_rows(const GraphDesc &g, int64_t base
     }
 }
 
-// hub rows: one CTA per chunk, FP64 partials, the last CTA of the row sums them in order
-__global__ void __launch_bounds__(kThreads) k_wdeg_hub(Ctx c) {
+// k_wdeg: weighted degrees D_ii = sum_j e_ij (+1) of the graphs that need them, then
+// D^-1/2 and the node table.
+//   hub rows   the CTA takes one chunk at a time: FP64 partial, and the last CTA of a
+//              row sums the partials in chunk order
+//   light rows then each warp claims row blocks: a group of lanes per row, 16-byte
+//              loads, Neumaier-compensated FP32 per lane, deterministic two-sum tree
+__global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int s_it;
     __shared__ double s_red[kThreads];
     __shared__ int s_last;
+    __shared__ GraphDesc wd[kWarps];
     const int tid = threadIdx.x;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
-    if (hub_chunks == 0) return;  // no row of any graph is long enough to be split
-    for (;;) {
+    while (hub_chunks > 0) {
         const int it = cta_claim(&c.cb.cs->ctr[3], &s_it);
         if ((uint32_t)it >= hub_chunks) break;
         const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
@@ -1138,12 +1189,6 @@ __global__ void __launch_bounds__(kThreads) k_wdeg_hub(Ctx c) {
             write_node(sg, he.row, (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
         }
     }
-}
-
-// light rows: a group of lanes per row, 16-byte loads, Neumaier-compensated FP32 per
-// lane, deterministic two-sum tree over the group
-__global__ void __launch_bounds__(kThreads) k_wdeg_rows(Ctx c) {
-    __shared__ GraphDesc wd[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cur = -1;
     for (;;) {
@@ -1309,6 +1354,12 @@ __device__ __forceinline__ RowTail row_tail(const GraphDesc &g, int64_t row) {
     return rt;
 }
 
+// Scale of a finished row: 1 / ||Z_i|| with the correlation option (rows with norm 0
+// keep scale 1, so they stay 0), else 1.  One division per row; entries are multiplied.
+__device__ __forceinline__ float row_scale(float ss, bool cor) {
+    return (cor && ss > 0.0f) ? 1.0f / sqrtf(ss) : 1.0f;
+}
+
 __device__ __forceinline__ float finish_entry(float total, int k, const RowTail &rt) {
     float v = total;
     if (rt.aug && k == rt.yi) v += rt.si;
@@ -1344,18 +1395,13 @@ __device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, i
         acc[k] = (k < K) ? finish_entry(acc[k], k, rt) : 0.0f;
         ss += acc[k] * acc[k];
     }
-    float r = 1.0f;
-    bool div = false;
-    if (rt.cor) {
-        r = sqrtf(ss);
-        div = r > 0.0f;
-    }
+    const float sc = row_scale(ss, rt.cor);
     float *z = g.Z + row * (int64_t)K;
     for (int k = gl; k < K; k += lpr) {
         float v = 0.0f;
 #pragma unroll
         for (int kk = 0; kk < KR; ++kk) v = (kk == k) ? acc[kk] : v;
-        z[k] = div ? v / r : v;
+        z[k] = v * sc;
     }
 }
 
@@ -1421,20 +1467,28 @@ __device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, 
     }
     for (int o = lpr >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (!active) return;
-    float r = 1.0f;
-    bool div = false;
-    if (rt.cor) {
-        r = sqrtf(ss);
-        div = r > 0.0f;
-    }
+    const float sc = row_scale(ss, rt.cor);
     float *z = g.Z + row * (int64_t)K;
-    for (int k = gl; k < K; k += lpr) {
+    auto take = [&](uint64_t m, int k) -> float {  // finished entry k of this lane, cleared
         float v = 0.0f;
-        if ((mine >> k) & 1ull) {
-            v = sacc[k * 32 + lane];
+        if (m & 1ull) {
+            v = sacc[k * 32 + lane] * sc;
             sacc[k * 32 + lane] = 0.0f;
         }
-        z[k] = div ? v / r : v;
+        return v;
+    };
+    if (lpr == 1 && (K & 3) == 0) {  // the lane writes its whole row: 16-byte stores
+        float4 *z4 = reinterpret_cast<float4 *>(z);
+        uint64_t m = mine;
+        for (int k = 0; k < K; k += 4, m >>= 4)
+            z4[k >> 2] = make_float4(take(m, k), take(m >> 1, k + 1), take(m >> 2, k + 2), take(m >> 3, k + 3));
+    } else if (lpr == 1 && (K & 1) == 0) {  // 8-byte stores
+        float2 *z2 = reinterpret_cast<float2 *>(z);
+        uint64_t m = mine;
+        for (int k = 0; k < K; k += 2, m >>= 2) z2[k >> 1] = make_float2(take(m, k), take(m >> 1, k + 1));
+    } else {
+        uint64_t m = mine >> gl;
+        for (int k = gl; k < K; k += lpr, m >>= lpr) z[k] = take(m, k);
     }
 }
 
@@ -1519,31 +1573,26 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
         wtot[kMaxK * kWarps - 1] = ss;
     }
     __syncthreads();
-    if (tid < K) {
-        const float ss = wtot[kMaxK * kWarps - 1];
-        float v = wtot[tid];
-        if (rt.cor) {
-            const float r = sqrtf(ss);
-            if (r > 0.0f) v = v / r;
-        }
-        g.Z[(int64_t)he.row * K + tid] = v;
-    }
+    if (tid < K) g.Z[(int64_t)he.row * K + tid] = wtot[tid] * row_scale(wtot[kMaxK * kWarps - 1], rt.cor);
 }
 
 constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
 
-// hub rows: one CTA per chunk
-__global__ void __launch_bounds__(kThreads) k_spmm_hub(Ctx c) {
+// k_spmm: Z with the fused epilogue.
+//   hub rows   the CTA takes one chunk at a time (two-sum partials; the last CTA of a
+//              row merges them in chunk order and runs the epilogue)
+//   light rows then persistent warps, each claiming blocks of rows_per_item rows
+__global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
     extern __shared__ __align__(16) float sacc_all[];
     __shared__ GraphDesc sg;
     __shared__ int s_it;
     __shared__ int s_last;
     __shared__ float wtot[kWarps * kMaxK];
+    __shared__ GraphDesc wd[kWarps];
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     const int H = (int)__ldcg(&c.cb.cs->hub_count);
-    if (hub_chunks == 0) return;  // no row of any graph is long enough to be split
     uint32_t err = 0;
-    for (;;) {
+    while (hub_chunks > 0) {
         const int it = cta_claim(&c.cb.cs->ctr[4], &s_it);
         if ((uint32_t)it >= hub_chunks) break;
         const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
@@ -1561,19 +1610,13 @@ __global__ void __launch_bounds__(kThreads) k_spmm_hub(Ctx c) {
             err = 0;
         }
     }
-}
-
-// light rows: persistent warps, each claiming blocks of rows_per_item rows
-__global__ void __launch_bounds__(kThreads) k_spmm_rows(Ctx c) {
-    extern __shared__ __align__(16) float sacc_all[];
-    __shared__ GraphDesc wd[kWarps];
+    __syncthreads();  // the chunks are done with the accumulator space
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *sacc = sacc_all + warp * kMaxK * 32;
     if (c.cb.kmax > kRegK)
         for (int i = lane; i < kMaxK * 32; i += 32) sacc[i] = 0.0f;
     __syncwarp();
     int cur = -1;
-    uint32_t err = 0;
     for (;;) {
         const uint32_t it = warp_claim(&c.cb.cs->ctr[5]);
         if (it >= (uint32_t)c.items) break;
@@ -1649,7 +1692,7 @@ cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st) {
 
 cudaError_t launch_prep(const Ctx &c, int blocks, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_prep<<<blocks, kThreads, 0, st>>>(c);
+    k_prep<<<blocks, kThreads, kIdRingBytes, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1678,7 +1721,7 @@ cudaError_t launch_scatter(const Ctx &c, int blocks, bool final_pass, int max_di
 
 cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_count<<<blocks, kThreads, 0, st>>>(c);
+    k_count<<<blocks, kThreads, kIdRingBytes, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1688,30 +1731,15 @@ cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_hubprep(const CallBufs &cb, cudaStream_t st) {
-    k_hubprep<<<1, kThreads, 0, st>>>(cb);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wdeg(const Ctx &c, int hub_blocks, int row_blocks, cudaStream_t st) {
-    if (hub_blocks > 0) {
-        k_wdeg_hub<<<hub_blocks, kThreads, 0, st>>>(c);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (row_blocks > 0) k_wdeg_rows<<<row_blocks, kThreads, 0, st>>>(c);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_spmm_hub(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_spmm_hub<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    k_wdeg<<<blocks, kThreads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmm_rows(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_spmm_rows<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    k_spmm<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1728,9 +1756,11 @@ cudaError_t configure_kernels() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_spmm_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+    e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdRingBytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+    e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdRingBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
 }
 
 static int occ(const void *f, size_t smem) {
@@ -1739,9 +1769,7 @@ static int occ(const void *f, size_t smem) {
     return n > 0 ? n : 1;
 }
 
-int occupancy_spmm_rows(bool smem_acc) { return occ((const void *)k_spmm_rows, smem_acc ? kSmemAccBytes : 0); }
-int occupancy_spmm_hub(bool smem_acc) { return occ((const void *)k_spmm_hub, smem_acc ? kSmemAccBytes : 0); }
-int occupancy_wdeg_rows() { return occ((const void *)k_wdeg_rows, 0); }
-int occupancy_wdeg_hub() { return occ((const void *)k_wdeg_hub, 0); }
+int occupancy_spmm(bool smem_acc) { return occ((const void *)k_spmm, smem_acc ? kSmemAccBytes : 0); }
+int occupancy_wdeg() { return occ((const void *)k_wdeg, 0); }
 
 }  // namespace gee

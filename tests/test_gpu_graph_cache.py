@@ -93,5 +93,5 @@ def test_timed_replay_reports_phases():
         if ran is None:
             ran = ph >= 0.0
         assert np.array_equal(ph >= 0.0, ran), f"call {it}: phases {ph}"
-    assert ran[gee.PHASES.index("k_scatter_final")] and ran[gee.PHASES.index("k_spmm_rows")]
+    assert ran[gee.PHASES.index("k_scatter_final")] and ran[gee.PHASES.index("k_spmm")]
     assert gee.gee_graph_cache_clear() == 0
