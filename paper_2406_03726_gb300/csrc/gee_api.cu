@@ -175,6 +175,7 @@ void layout_call_zero(Bump &b, CallBufs &cb) {
 void layout_call_rest(Bump &b, CallBufs &cb) {
     cb.hubs = b.take<HubEntry>(cb.hub_cap);
     cb.chunk_off = b.take<uint32_t>((size_t)cb.hub_cap + 1);
+    cb.chunk_hub = b.take<uint32_t>(cb.chunk_cap);
     cb.part_deg = b.take<double>(cb.chunk_cap);
     cb.part_z = b.take<float2>((size_t)cb.chunk_cap * (size_t)cb.kmax);
 }

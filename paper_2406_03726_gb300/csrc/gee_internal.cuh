@@ -91,6 +91,7 @@ struct CallBufs {
     CallState *cs;           // zeroed
     HubEntry *hubs;          // [hub_cap]
     uint32_t *chunk_off;     // [hub_cap + 1]
+    uint32_t *chunk_hub;     // [chunk_cap]   hub of each chunk
     uint32_t *arrive_deg;    // [hub_cap] zeroed
     uint32_t *arrive_z;      // [hub_cap] zeroed
     double *part_deg;        // [chunk_cap]

@@ -906,7 +906,11 @@ __device__ void hub_chunk_offsets(const CallBufs &cb, uint32_t *s_scan) {
         const uint32_t v = h < H ? (uint32_t)__ldcg(&cb.hubs[h].nch) : 0u;
         uint32_t tot;
         const uint32_t x = block_excl_scan(v, s_scan, tot);
-        if (h < H) cb.chunk_off[h] = base_run + x;
+        if (h < H) {
+            const uint32_t o = base_run + x;
+            cb.chunk_off[h] = o;
+            for (uint32_t k = 0; k < v && o + k < cb.chunk_cap; ++k) cb.chunk_hub[o + k] = h;
+        }
         base_run += tot;
     }
     if (threadIdx.x == 0) {
@@ -1001,15 +1005,6 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     }
 }
 
-__device__ __forceinline__ int find_hub(const uint32_t *off, int H, uint32_t item) {
-    int lo = 0, hi = H;  // largest h with off[h] <= item
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (__ldcg(off + mid) <= item) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
 
 // Work item claiming.  CTA-level (hub chunks, which need the whole CTA) and warp-level
 // (light rows: every warp claims and finishes its own rows, with no CTA barrier, so a
@@ -1103,20 +1098,47 @@ __device__ __forceinline__ uint32_t warp_sort32(uint32_t key, int lane) {
 
 constexpr uint32_t kNoRow = 0xffffffffu;
 
-// Sorted (class << 5 | offset) keys of the block's rows; kNoRow for rows to skip.
-__device__ __forceinline__ uint32_t sorted_row_keys(const GraphDesc &g, int64_t base, int nrows, int lane) {
-    uint32_t key = kNoRow;
+// What a pass needs of a row, read once per block: lane l holds row base + l.
+struct BlockRow {
+    int32_t rs, re;  // CSR entries [rs, re) (empty for no row)
+    int2 tab;        // k_spmm: node table entry {y_i, s_i} of the row
+    float dinv;      // k_spmm: D_ii^-1/2 (1 without the Laplacian)
+    int y, ny;       // k_wdeg: label y_i and class size n_{y_i}
+};
+
+// Loads the block's rows (one round trip, two for k_wdeg's class sizes) and returns the
+// sorted (class << 5 | offset) keys; kNoRow for rows to skip (none, or hub rows).
+template <bool SPMM>
+__device__ __forceinline__ uint32_t load_block_rows(const GraphDesc &g, int64_t base, int nrows, int lane,
+                                                    BlockRow &br) {
     const int64_t row = base + lane;
-    if (lane < nrows && row < g.N) {
-        int64_t rs, re;
-        row_range(g, row, rs, re);
-        if (re - rs <= g.hub_C) key = (lanes_log2_for(re - rs) << 5) | (uint32_t)lane;
+    const bool has = lane < nrows && row < g.N;
+    br.rs = br.re = 0;
+    br.tab = make_int2(0, 0);
+    br.dinv = 1.0f;
+    br.y = -1;
+    br.ny = 0;
+    if (has) {
+        const int32_t a = __ldcg(g.rowptr + row), b = __ldcg(g.rowptr + row + 1);
+        if (SPMM) {
+            br.tab = __ldg(g.tab + row);
+            if (g.flags & kOptLap) br.dinv = __ldg(g.dinv + row);
+        } else {
+            br.y = __ldg(g.y + row);
+        }
+        const int32_t E32 = (int32_t)g.E;
+        br.rs = min(max(a, 0), E32);
+        br.re = min(max(b, br.rs), E32);
     }
+    if (!SPMM && br.y >= 0 && br.y < g.K) br.ny = __ldcg(g.nk + br.y);
+    uint32_t key = kNoRow;
+    if (has && br.re - br.rs <= g.hub_C) key = (lanes_log2_for(br.re - br.rs) << 5) | (uint32_t)lane;
     return warp_sort32(key, lane);
 }
 
-// Run f(row, lane-in-group, lanes-per-row) over the block, one round per group of rows
-// of a class; every lane of the warp takes part in every round (row = N when idle).
+// Run f(row, lane-in-group, lanes-per-row, lane of the row's BlockRow) over the block,
+// one round per group of rows of a class; every lane of the warp takes part in every
+// round (row = N when idle).
 template <class F>
 __device__ __forceinline__ void for_sorted_rows(const GraphDesc &g, int64_t base, uint32_t sk, int lane, F &&f) {
     const int nvalid = __popc(__ballot_sync(0xffffffffu, sk != kNoRow));
@@ -1129,8 +1151,8 @@ __device__ __forceinline__ void for_sorted_rows(const GraphDesc &g, int64_t base
         for (int j = 0; j < n_c; j += rpr) {
             const int idx = pos + j + grp;
             const uint32_t k = __shfl_sync(0xffffffffu, sk, min(idx, 31));
-            const int64_t row = (idx < pos + n_c) ? base + (int64_t)(k & 31u) : (int64_t)g.N;
-            f(row, gl, lpr);
+            const bool on = idx < pos + n_c;
+            f(on ? base + (int64_t)(k & 31u) : (int64_t)g.N, gl, lpr, on ? (int)(k & 31u) : 0);
         }
         pos += n_c;
     }
@@ -1150,11 +1172,10 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
     __shared__ GraphDesc wd[kWarps];
     const int tid = threadIdx.x;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
-    const int H = (int)__ldcg(&c.cb.cs->hub_count);
     while (hub_chunks > 0) {
         const int it = cta_claim(&c.cb.cs->ctr[3], &s_it);
         if ((uint32_t)it >= hub_chunks) break;
-        const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
+        const int hub = (int)__ldcg(c.cb.chunk_hub + it);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
         load_desc_idx(c, he.g, &sg);
@@ -1204,13 +1225,14 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
         const GraphDesc &sg = wd[warp];
         if (!sg.wdeg) continue;
         const int64_t base = (int64_t)blk * sg.rows_per_item;
-        const uint32_t sk = sorted_row_keys(sg, base, sg.rows_per_item, lane);
-        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr) {
+        BlockRow br;
+        const uint32_t sk = load_block_rows<false>(sg, base, sg.rows_per_item, lane, br);
+        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr, int bi) {
+            const int64_t rs = __shfl_sync(0xffffffffu, br.rs, bi), re = __shfl_sync(0xffffffffu, br.re, bi);
+            const int yv = __shfl_sync(0xffffffffu, br.y, bi), ny = __shfl_sync(0xffffffffu, br.ny, bi);
             float s = 0.f, cc = 0.f;
             bool active = false;
             if (row < sg.N) {
-                int64_t rs, re;
-                row_range(sg, row, rs, re);
                 active = true;
                 const int64_t a0 = rs & ~(int64_t)3;
                 const int64_t step = 4 * (int64_t)lpr;
@@ -1241,7 +1263,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
             }
             if (active && gl == 0) {
                 const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
-                write_node(sg, row, (s + cc) + aug, (sg.flags & kOptLap) != 0);
+                write_node_known(sg, row, (s + cc) + aug, (sg.flags & kOptLap) != 0, yv, ny);
             }
         });
     }
@@ -1342,15 +1364,14 @@ struct RowTail {
     bool aug, lap, cor;
 };
 
-__device__ __forceinline__ RowTail row_tail(const GraphDesc &g, int64_t row) {
+__device__ __forceinline__ RowTail row_tail(const GraphDesc &g, int2 ti, float dinv) {
     RowTail rt;
-    const int2 ti = __ldg(g.tab + row);
     rt.yi = ti.x;
     rt.si = __int_as_float(ti.y);
     rt.aug = (g.flags & kOptAug) != 0;
     rt.lap = (g.flags & kOptLap) != 0;
     rt.cor = (g.flags & kOptCor) != 0;
-    rt.dv = rt.lap ? __ldg(g.dinv + row) : 1.0f;
+    rt.dv = rt.lap ? dinv : 1.0f;
     return rt;
 }
 
@@ -1369,25 +1390,20 @@ __device__ __forceinline__ float finish_entry(float total, int k, const RowTail 
 
 // one light row per lane group, K <= 8: register accumulators, butterfly over the group
 template <int KR>
-__device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, int gl, int lpr, uint32_t &err) {
+__device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, int64_t rs, int64_t re,
+                                              const RowTail &rt, int gl, int lpr, uint32_t &err) {
     float acc[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
-    bool active = false;
-    if (row < g.N) {
-        int64_t rs, re;
-        row_range(g, row, rs, re);
-        if (re - rs <= g.hub_C) {
-            active = true;
-            if (lpr == 32) acc_reg<KR, 4>(g, rs, re, gl, lpr, acc, err);
-            else acc_reg<KR, 2>(g, rs, re, gl, lpr, acc, err);
-        }
+    const bool active = row < g.N;
+    if (active) {
+        if (lpr == 32) acc_reg<KR, 4>(g, rs, re, gl, lpr, acc, err);
+        else acc_reg<KR, 2>(g, rs, re, gl, lpr, acc, err);
     }
 #pragma unroll
     for (int k = 0; k < KR; ++k)
         for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
     if (!active) return;
-    const RowTail rt = row_tail(g, row);
     const int K = g.K;
     float ss = 0.0f;
 #pragma unroll
@@ -1423,24 +1439,16 @@ __device__ __forceinline__ uint64_t owned_classes(int gl, int lpr) {
     return m << gl;
 }
 
-__device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, int gl, int lpr, float *sacc,
-                                               int lane, uint32_t &err) {
+__device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, int64_t rs, int64_t re,
+                                               const RowTail &rt, int gl, int lpr, float *sacc, int lane,
+                                               uint32_t &err) {
     const int K = g.K;
     const int g0 = lane - gl;
     uint32_t tlo = 0, thi = 0;
-    bool active = false;
-    if (row < g.N) {
-        int64_t rs, re;
-        row_range(g, row, rs, re);
-        if (re - rs <= g.hub_C) {
-            active = true;
-            if (lpr == 32) acc_smem<4>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
-            else acc_smem<2>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
-        }
-    }
-    RowTail rt;
+    const bool active = row < g.N;
     if (active) {
-        rt = row_tail(g, row);
+        if (lpr == 32) acc_smem<4>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
+        else acc_smem<2>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
         if (rt.aug) {  // the augmentation term lands on the row's own class
             if (rt.yi < 32) tlo |= 1u << rt.yi;
             else thi |= 1u << (rt.yi - 32);
@@ -1553,7 +1561,7 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
     if (!*s_last) return;
     __threadfence();
     // last chunk to finish: merge all chunks of the row in chunk order
-    const RowTail rt = row_tail(g, he.row);
+    const RowTail rt = row_tail(g, __ldg(g.tab + he.row), (g.flags & kOptLap) ? __ldg(g.dinv + he.row) : 1.0f);
     if (tid < K) {
         float S = 0.0f, C = 0.0f;
         for (int ch = 0; ch < he.nch; ++ch) {
@@ -1582,7 +1590,7 @@ constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
 //   hub rows   the CTA takes one chunk at a time (two-sum partials; the last CTA of a
 //              row merges them in chunk order and runs the epilogue)
 //   light rows then persistent warps, each claiming blocks of rows_per_item rows
-__global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
+__global__ void __launch_bounds__(kThreads, 3) k_spmm(Ctx c) {
     extern __shared__ __align__(16) float sacc_all[];
     __shared__ GraphDesc sg;
     __shared__ int s_it;
@@ -1590,12 +1598,11 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
     __shared__ float wtot[kWarps * kMaxK];
     __shared__ GraphDesc wd[kWarps];
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
-    const int H = (int)__ldcg(&c.cb.cs->hub_count);
     uint32_t err = 0;
     while (hub_chunks > 0) {
         const int it = cta_claim(&c.cb.cs->ctr[4], &s_it);
         if ((uint32_t)it >= hub_chunks) break;
-        const int hub = find_hub(c.cb.chunk_off, H, (uint32_t)it);
+        const int hub = (int)__ldcg(c.cb.chunk_hub + it);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
         load_desc_idx(c, he.g, &sg);
@@ -1630,13 +1637,19 @@ __global__ void __launch_bounds__(kThreads) k_spmm(Ctx c) {
         const GraphDesc &sg = wd[warp];
         const int K = sg.K;
         const int64_t base = (int64_t)blk * sg.rows_per_item;
-        const uint32_t sk = sorted_row_keys(sg, base, sg.rows_per_item, lane);
-        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr) {
-            if (K <= 1) light_row_reg<1>(sg, row, gl, lpr, err);
-            else if (K <= 2) light_row_reg<2>(sg, row, gl, lpr, err);
-            else if (K <= 4) light_row_reg<4>(sg, row, gl, lpr, err);
-            else if (K <= 8) light_row_reg<8>(sg, row, gl, lpr, err);
-            else light_row_smem(sg, row, gl, lpr, sacc, lane, err);
+        BlockRow br;
+        const uint32_t sk = load_block_rows<true>(sg, base, sg.rows_per_item, lane, br);
+        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr, int bi) {
+            const int64_t rs = __shfl_sync(0xffffffffu, br.rs, bi), re = __shfl_sync(0xffffffffu, br.re, bi);
+            int2 t;
+            t.x = __shfl_sync(0xffffffffu, br.tab.x, bi);
+            t.y = __shfl_sync(0xffffffffu, br.tab.y, bi);
+            const RowTail rt = row_tail(sg, t, __shfl_sync(0xffffffffu, br.dinv, bi));
+            if (K <= 1) light_row_reg<1>(sg, row, rs, re, rt, gl, lpr, err);
+            else if (K <= 2) light_row_reg<2>(sg, row, rs, re, rt, gl, lpr, err);
+            else if (K <= 4) light_row_reg<4>(sg, row, rs, re, rt, gl, lpr, err);
+            else if (K <= 8) light_row_reg<8>(sg, row, rs, re, rt, gl, lpr, err);
+            else light_row_smem(sg, row, rs, re, rt, gl, lpr, sacc, lane, err);
         });
         if (err) {
             atomicOr(sg.status, err);
