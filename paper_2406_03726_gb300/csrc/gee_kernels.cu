@@ -1022,6 +1022,13 @@ __device__ __forceinline__ uint32_t warp_claim(uint32_t *ctr) {
     return __shfl_sync(0xffffffffu, it, 0);
 }
 
+// Work items of persistent CTAs / warps: the first item of each is its own index (no
+// atomic: thousands of warps starting at once would queue on one counter), later ones
+// come from the counter, offset past those first items.
+__device__ __forceinline__ uint32_t warp_first_item() { return blockIdx.x * kWarps + (threadIdx.x >> 5); }
+__device__ __forceinline__ uint32_t warp_next_item(uint32_t *ctr) { return warp_claim(ctr) + gridDim.x * kWarps; }
+__device__ __forceinline__ int cta_next_item(uint32_t *ctr, int *s_it) { return cta_claim(ctr, s_it) + (int)gridDim.x; }
+
 // Copy graph g's descriptor into this warp's shared slot.
 __device__ __forceinline__ void warp_load_desc(const Ctx &c, int g, GraphDesc *slot) {
     const int lane = threadIdx.x & 31;
@@ -1172,9 +1179,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
     __shared__ GraphDesc wd[kWarps];
     const int tid = threadIdx.x;
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
-    while (hub_chunks > 0) {
-        const int it = cta_claim(&c.cb.cs->ctr[3], &s_it);
-        if ((uint32_t)it >= hub_chunks) break;
+    for (int it = blockIdx.x; (uint32_t)it < hub_chunks; it = cta_next_item(&c.cb.cs->ctr[3], &s_it)) {
         const int hub = (int)__ldcg(c.cb.chunk_hub + it);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
@@ -1212,9 +1217,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cur = -1;
-    for (;;) {
-        const uint32_t it = warp_claim(&c.cb.cs->ctr[6]);
-        if (it >= (uint32_t)c.items) break;
+    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items; it = warp_next_item(&c.cb.cs->ctr[6])) {
         int blk;
         const int g = warp_item_graph(c, it, blk);
         if (g != cur) {
@@ -1599,9 +1602,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_spmm(Ctx c) {
     __shared__ GraphDesc wd[kWarps];
     const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
     uint32_t err = 0;
-    while (hub_chunks > 0) {
-        const int it = cta_claim(&c.cb.cs->ctr[4], &s_it);
-        if ((uint32_t)it >= hub_chunks) break;
+    for (int it = blockIdx.x; (uint32_t)it < hub_chunks; it = cta_next_item(&c.cb.cs->ctr[4], &s_it)) {
         const int hub = (int)__ldcg(c.cb.chunk_hub + it);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
@@ -1624,9 +1625,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_spmm(Ctx c) {
         for (int i = lane; i < kMaxK * 32; i += 32) sacc[i] = 0.0f;
     __syncwarp();
     int cur = -1;
-    for (;;) {
-        const uint32_t it = warp_claim(&c.cb.cs->ctr[5]);
-        if (it >= (uint32_t)c.items) break;
+    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items; it = warp_next_item(&c.cb.cs->ctr[5])) {
         int blk;
         const int g = warp_item_graph(c, it, blk);
         if (g != cur) {
