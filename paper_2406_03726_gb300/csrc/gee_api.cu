@@ -131,7 +131,7 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
     // rows a warp claims at once: whole 32-row blocks sorted by length, or two rows when
     // the rows are long enough that each takes the whole warp anyway
-    d.rows_per_item = lpr >= 32 ? 2 : 32;
+    d.rows_per_item = lpr >= 32 ? 1 : 32;
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
     // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
     // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
