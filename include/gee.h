@@ -79,9 +79,27 @@ typedef struct gee_opts {
     uint32_t flags;        /* GEE_DIAG_AUG | GEE_LAPLACIAN | GEE_CORRELATION */
     int32_t hub_threshold; /* rows with more entries are split into chunks of this many
                               entries across CTAs and merged; 0 = automatic */
-    int32_t lanes_per_row; /* threads cooperating on one light row: 1,2,4,...,32; 0 = auto */
-    int32_t reserved;      /* must be 0 */
+    int32_t lanes_per_row; /* graph-level lanes per light row (1,2,...,32; 0 = auto from the
+                              mean degree): sets the automatic threshold (256 x lanes) */
+    int32_t rows_per_item; /* light rows a warp claims at once: 1,2,4,...,32; 0 = auto */
 } gee_opts;
+
+/*
+ * gee_autotune -- chooses hub_threshold and rows_per_item for one graph by running
+ * gee_embed with a small set of candidates around the automatic values and timing
+ * each with CUDA events on `stream` (the call waits for the stream).  The fastest
+ * candidate goes to *best (flags copied from opts->flags; a tuning field of opts that
+ * is already non-zero is kept fixed), its mean time in ms to *best_ms (may be NULL).
+ * Arguments as for gee_embed; the workspace must hold
+ * gee_autotune_workspace_size(...) bytes.  Z is overwritten (with a correct result).
+ * The choice is cached per (device, N, E, K, weighted, flags, fixed fields): a repeated
+ * call returns it without running anything.  Tuning changes only the order of
+ * floating-point additions, never which value is computed.  Returns GEE_OK or an error.
+ */
+size_t gee_autotune_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts);
+int gee_autotune(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                 const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
+                 size_t workspace_bytes, void *stream, gee_opts *best, float *best_ms);
 
 /* Bytes of device workspace gee_embed needs for a graph of this size.  `weighted` is
  * non-zero when a weight array will be passed.  opts may be NULL (defaults). */

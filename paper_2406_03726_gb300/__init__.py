@@ -32,6 +32,8 @@ from ._native import (  # noqa: F401
     gee_embed_host,
     gee_embed_static,
     gee_graph_cache_clear,
+    gee_autotune,
+    gee_autotune_workspace_size,
     gee_embed_timed,
     gee_host_workspace_size,
     gee_opts,
@@ -84,12 +86,12 @@ def workspace(E, N, K, weighted, opts=None, device=None):
 
 
 def embed(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, ws=None, Z=None,
-          status=None, stream=None):
+          status=None, stream=None, rows_per_item=0):
     """Z (float32 [N, K], on the device of ``src``) from device tensors.  ``status`` may be a
     uint32 device tensor of one element receiving the GEE_STATUS_* bits."""
     import torch
     E = int(src.numel())
-    opts = make_opts(flags, hub_threshold, lanes_per_row)
+    opts = make_opts(flags, hub_threshold, lanes_per_row, rows_per_item)
     dev = labels.device
     if Z is None:
         Z = torch.empty((N, K), dtype=torch.float32, device=dev)
@@ -98,6 +100,24 @@ def embed(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, 
     rc = gee_embed(src, dst, w, E, N, labels, K, opts, Z, ws, ws.numel(), stream, status)
     _check(rc, "gee_embed")
     return Z
+
+
+def autotune(src, dst, w, N, labels, K, flags=0, stream=None):
+    """(opts, ms): the split threshold and rows per work item gee_autotune picks for this
+    graph (a gee_opts with ``flags``), and the mean call time it measured."""
+    import ctypes
+    import torch
+    E = int(src.numel())
+    opts = make_opts(flags)
+    n = gee_autotune_workspace_size(E, N, K, w is not None, opts)
+    if n == 0:
+        raise GeeError(1, "gee_autotune_workspace_size")
+    ws = torch.empty(n, dtype=torch.uint8, device=labels.device)
+    Z = torch.empty((N, K), dtype=torch.float32, device=labels.device)
+    best = make_opts(flags)
+    ms = ctypes.c_float(0.0)
+    _check(gee_autotune(src, dst, w, E, N, labels, K, opts, Z, ws, n, stream, best, ms), "gee_autotune")
+    return best, float(ms.value)
 
 
 def build_csr(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, status=None, stream=None):

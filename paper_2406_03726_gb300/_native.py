@@ -15,7 +15,7 @@ _I32, _I64, _U32, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.
 
 class gee_opts(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("hub_threshold", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("rows_per_item", ctypes.c_int32)]
 
 
 class gee_graph(ctypes.Structure):
@@ -53,6 +53,8 @@ _SIGNATURES = {
     "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
     "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "gee_graph_cache_clear": ([], ctypes.c_int),
+    "gee_autotune_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_autotune": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P, _P], ctypes.c_int),
     "gee_batch_workspace_size": ([_P, _I32, _P], _SZ),
     "gee_embed_batch": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
     "gee_batch_plan_create": ([_P, _I32, _P, _P, _SZ, _P, _P], ctypes.c_int),
@@ -120,8 +122,8 @@ def stream_handle(stream):
     return stream.cuda_stream
 
 
-def make_opts(flags=0, hub_threshold=0, lanes_per_row=0):
-    return gee_opts(flags, hub_threshold, lanes_per_row, 0)
+def make_opts(flags=0, hub_threshold=0, lanes_per_row=0, rows_per_item=0):
+    return gee_opts(flags, hub_threshold, lanes_per_row, rows_per_item)
 
 
 def _opts_ref(opts):
@@ -182,6 +184,19 @@ def gee_embed_host(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_b
 def gee_embed_static(src, dst, w, E, N, labels, K, opts, Z, stream=None, d_status=None) -> int:
     return lib().gee_embed_static(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
                                   stream_handle(stream), ptr(d_status))
+
+
+def gee_autotune_workspace_size(E, N, K, weighted, opts=None) -> int:
+    return lib().gee_autotune_workspace_size(E, N, K, 1 if weighted else 0, _opts_ref(opts))
+
+
+def gee_autotune(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_bytes, stream=None, best=None,
+                 best_ms=None) -> int:
+    """best: a gee_opts to fill; best_ms: a ctypes.c_float or None."""
+    return lib().gee_autotune(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(Z),
+                              ptr(workspace), workspace_bytes, stream_handle(stream),
+                              ctypes.byref(best) if best is not None else None,
+                              ctypes.byref(best_ms) if best_ms is not None else None)
 
 
 def gee_graph_cache_clear() -> int:

@@ -40,6 +40,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kSMs = 152;                   // GB300
 constexpr size_t kSmemPerSM = 228 * 1024;   // shared memory per SM usable by CTAs
+constexpr int kWarpsPerSM = 24;             // resident warps of the row kernels (3 CTAs)
 
 struct DeviceInfo {
     bool ready = false;
@@ -129,9 +130,19 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
     d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
-    // rows a warp claims at once: whole 32-row blocks sorted by length, or two rows when
-    // the rows are long enough that each takes the whole warp anyway
-    d.rows_per_item = lpr >= 32 ? 1 : 32;
+    // rows a warp claims at once: blocks of up to 32 rows sorted by length, one row when
+    // the rows are long enough that each takes the whole warp anyway, and small enough
+    // blocks that a graph of few rows still gives every resident warp some work
+    if (o.rows_per_item > 0) {
+        d.rows_per_item = o.rows_per_item;
+    } else if (lpr >= 32) {
+        d.rows_per_item = 1;
+    } else {
+        const int64_t warps = (int64_t)kSMs * kWarpsPerSM;
+        int rpi = 32;
+        while (rpi > 1 && (int64_t)s.N < 2 * warps * rpi) rpi >>= 1;
+        d.rows_per_item = rpi;
+    }
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
     // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
     // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
@@ -194,8 +205,9 @@ gee_opts opts_or_default(const gee_opts *o) {
 }
 
 int check_opts(const gee_opts &o) {
-    if (o.reserved != 0 || o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
-        (o.lanes_per_row & (o.lanes_per_row - 1)))
+    if (o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
+        (o.lanes_per_row & (o.lanes_per_row - 1)) || o.rows_per_item < 0 || o.rows_per_item > 32 ||
+        (o.rows_per_item & (o.rows_per_item - 1)))
         return GEE_ERR_ARG;
     return GEE_OK;
 }
@@ -604,6 +616,152 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
               size_t workspace_bytes, void *stream, uint32_t *d_status) {
     return embed_impl(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, d_workspace, workspace_bytes, stream,
                       d_status, nullptr, nullptr);
+}
+
+}  // extern "C"
+
+// ---- autotuner --------------------------------------------------------------------------
+namespace gee {
+namespace {
+
+struct TuneEntry {
+    int device;
+    int64_t E;
+    int32_t N, K;
+    int weighted;
+    gee_opts fixed;  // the caller's opts (flags and the fields it fixed)
+    gee_opts best;
+    float ms;
+};
+
+std::mutex g_tune_mu;
+std::vector<TuneEntry> *g_tune = nullptr;  // never freed
+
+bool same_opts(const gee_opts &a, const gee_opts &b) {
+    return a.flags == b.flags && a.hub_threshold == b.hub_threshold && a.lanes_per_row == b.lanes_per_row &&
+           a.rows_per_item == b.rows_per_item;
+}
+
+// Split thresholds and row-block sizes around the automatic ones (the caller's non-zero
+// fields stay fixed).
+std::vector<gee_opts> tune_candidates(const Shape &s, const gee_opts &o) {
+    GraphDesc d;
+    std::memset(&d, 0, sizeof(d));
+    plan_params(s, o, false, d);
+    std::vector<int32_t> hubs, rpis;
+    auto add = [](std::vector<int32_t> &v, int32_t x) {
+        if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+    };
+    if (o.hub_threshold > 0) {
+        add(hubs, o.hub_threshold);
+    } else {
+        add(hubs, d.hub_C);
+        add(hubs, std::max(1024, d.hub_C / 2));
+        add(hubs, d.hub_C * 2);
+    }
+    if (o.rows_per_item > 0) {
+        add(rpis, o.rows_per_item);
+    } else {
+        add(rpis, d.rows_per_item);
+        add(rpis, std::max(1, d.rows_per_item / 4));
+        add(rpis, std::min(32, d.rows_per_item * 4));
+    }
+    std::vector<gee_opts> out;
+    for (int32_t h : hubs)
+        for (int32_t r : rpis) {
+            gee_opts c = o;
+            c.hub_threshold = h;
+            c.rows_per_item = r;
+            out.push_back(c);
+        }
+    return out;
+}
+
+}  // namespace
+}  // namespace gee
+
+extern "C" {
+
+size_t gee_autotune_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts) {
+    if (check_shape(E, N, K) != GEE_OK) return 0;
+    const gee_opts o = opts_or_default(opts);
+    size_t m = 0;
+    for (const gee_opts &c : tune_candidates(Shape{E, N, K, weighted != 0}, o))
+        m = std::max(m, gee_workspace_size(E, N, K, weighted, &c));
+    return m;
+}
+
+int gee_autotune(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                 const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
+                 size_t workspace_bytes, void *stream, gee_opts *best, float *best_ms) {
+    if (!best) return GEE_ERR_ARG;
+    GEE_TRY(check_shape(E, N, K));
+    const gee_opts o = opts_or_default(opts);
+    GEE_TRY(check_opts(o));
+    int dev = 0;
+    GEE_TRY(cuda_check(cudaGetDevice(&dev)));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune)
+            for (const TuneEntry &t : *g_tune)
+                if (t.device == dev && t.E == E && t.N == N && t.K == K && t.weighted == (d_w != nullptr) &&
+                    same_opts(t.fixed, o)) {
+                    *best = t.best;
+                    if (best_ms) *best_ms = t.ms;
+                    return GEE_OK;
+                }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GEE_TRY(cuda_check(cudaEventCreate(&e0)));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GEE_ERR_CUDA;
+    }
+    constexpr int kReps = 3;
+    int rc = GEE_OK;
+    float best_t = -1.0f;
+    gee_opts pick = o;
+    for (const gee_opts &c : tune_candidates(Shape{E, N, K, d_w != nullptr}, o)) {
+        if (gee_workspace_size(E, N, K, d_w != nullptr, &c) > workspace_bytes) continue;
+        gee_opts run = c;
+        run.flags |= GEE_NO_GRAPH_CACHE;  // the candidates do not fill the launch cache
+        rc = gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes, stream,
+                       nullptr);  // warm-up
+        if (rc == GEE_OK) rc = cuda_check(cudaEventRecord(e0, st));
+        for (int i = 0; i < kReps && rc == GEE_OK; ++i)
+            rc = gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes, stream,
+                           nullptr);
+        if (rc == GEE_OK) rc = cuda_check(cudaEventRecord(e1, st));
+        if (rc == GEE_OK) rc = cuda_check(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        if (rc == GEE_OK) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1));
+        if (rc != GEE_OK) break;
+        ms /= kReps;
+        if (best_t < 0.0f || ms < best_t) {
+            best_t = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GEE_OK) return rc;
+    if (best_t < 0.0f) return GEE_ERR_WORKSPACE;  // no candidate fits the workspace
+    *best = pick;
+    if (best_ms) *best_ms = best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune) g_tune = new std::vector<TuneEntry>();
+    TuneEntry t;
+    t.device = dev;
+    t.E = E;
+    t.N = N;
+    t.K = K;
+    t.weighted = d_w != nullptr;
+    t.fixed = o;
+    t.best = pick;
+    t.ms = best_t;
+    g_tune->push_back(t);
+    return GEE_OK;
 }
 
 int gee_graph_cache_clear(void) {

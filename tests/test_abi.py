@@ -65,3 +65,18 @@ def test_argument_errors_need_no_gpu(lib):
     assert gee.gee_embed(None, None, None, 0, 5, 1, 0, None, 1, None, 0) == 1                 # K = 0
     assert gee.gee_embed(None, None, None, 0, 1 << 22, 1, 3, None, 1, None, 0) == 2           # N too large
     assert gee.gee_class_counts(None, None, 5, None, 3, None) == 1
+
+
+def test_tuning_fields_checked_on_host(lib):
+    import paper_2406_03726_gb300 as gee
+    # rows_per_item and lanes_per_row must be powers of two up to 32
+    for bad in (gee.make_opts(7, 0, 0, 3), gee.make_opts(7, 0, 0, 64), gee.make_opts(7, 0, 5, 0),
+                gee.make_opts(7, -1, 0, 0)):
+        assert gee.gee_embed(1, 1, None, 4, 5, 1, 3, bad, 1, 1, 1 << 20) == 1
+    # the autotuner's workspace covers every candidate, so it is at least the plain one
+    for E, N, K, w in ((11_124_844, 10_000, 3, True), (20_000_000, 600_000, 50, False), (100, 10, 2, True)):
+        assert gee.gee_autotune_workspace_size(E, N, K, w) >= gee.gee_workspace_size(E, N, K, w)
+    assert gee.gee_autotune_workspace_size(10, 1 << 22, 3, False) == 0
+    best = gee.make_opts(7)
+    assert gee.gee_autotune(None, None, None, 10, 5, None, 3, None, None, None, 0, None, None) == 1  # no best
+    assert gee.gee_autotune(None, None, None, 0, 1 << 22, 1, 3, None, 1, 1, 0, None, best) == 2     # N too large
