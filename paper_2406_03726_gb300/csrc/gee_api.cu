@@ -101,9 +101,14 @@ struct Shape {
     bool weighted;
 };
 
-// Plan parameters that depend only on the graph and the options (never on the batch
-// it is part of, so a graph gives the same bits alone and in a batch).
-void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d) {
+// Plan parameters of one graph.  Everything that decides the order of floating-point
+// additions depends only on the graph and the options (never on the batch it is part of,
+// so a graph gives the same bits alone and in a batch); the row-block size only groups
+// rows into work items.
+// rows_in_launch: rows of every graph the launch covers (N alone for a single graph);
+// the automatic row-block size keeps the launch's warps busy, not each graph's.
+void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d, int64_t rows_in_launch = -1) {
+    if (rows_in_launch < 0) rows_in_launch = s.N;
     d.E = s.E;
     d.N = s.N;
     d.K = s.K;
@@ -130,17 +135,15 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d)
     d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
     d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
     d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
-    // rows a warp claims at once: blocks of up to 32 rows sorted by length, one row when
-    // the rows are long enough that each takes the whole warp anyway, and small enough
-    // blocks that a graph of few rows still gives every resident warp some work
+    // rows a warp claims at once: blocks of up to 32 rows sorted by length, small enough
+    // that a launch of few rows still gives every resident warp two blocks (a row's lanes
+    // come from its length, so short rows share a warp in any block)
     if (o.rows_per_item > 0) {
         d.rows_per_item = o.rows_per_item;
-    } else if (lpr >= 32) {
-        d.rows_per_item = 1;
     } else {
         const int64_t warps = (int64_t)kSMs * kWarpsPerSM;
         int rpi = 32;
-        while (rpi > 1 && (int64_t)s.N < 2 * warps * rpi) rpi >>= 1;
+        while (rpi > 1 && rows_in_launch < 2 * warps * rpi) rpi >>= 1;
         d.rows_per_item = rpi;
     }
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
@@ -960,11 +963,15 @@ int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base
     std::memset(&cb, 0, sizeof(cb));
     cb.kmax = 1;
     uint64_t hub_cap = 0, chunk_cap = 0;
+    int64_t rows = 0;
     for (int32_t g = 0; g < G; ++g) {
         GEE_TRY(check_graph(graphs[g]));
+        rows += graphs[g].N;
+    }
+    for (int32_t g = 0; g < G; ++g) {
         GraphDesc &d = L.descs[g];
         std::memset(&d, 0, sizeof(d));
-        plan_params(Shape{graphs[g].E, graphs[g].N, graphs[g].K, graphs[g].w != nullptr}, o, false, d);
+        plan_params(Shape{graphs[g].E, graphs[g].N, graphs[g].K, graphs[g].w != nullptr}, o, false, d, rows);
         // ranges of at least 8 tiles (one CTA each, many graphs in flight); never more
         // ranges than the graph alone would use, so a batch needs no more workspace
         // than its graphs would separately.  Only how work is cut changes, never Z.
