@@ -34,6 +34,7 @@ METRIC = "GEE edges/s and % HBM roofline (all options on); p50/p99 served latenc
 UNIT = "edges/s"
 ALL_OPTIONS = 7
 L2_FLUSH_BYTES = 256 << 20
+ONE_PASS_BITS = 8  # graphs with node ids of at most this many bits are sorted in one radix pass
 KERNEL_TIMING_STEPS = 50
 
 WORKLOADS = {
@@ -71,7 +72,7 @@ def kernel_bytes(g):
     read or write once, nothing for re-reads or L2-resident gathers."""
     E, N, K = g.E, g.N, g.K
     wt = 1 if g.w is not None else 0
-    two = (N - 1).bit_length() > 11
+    two = max(1, (N - 1).bit_length()) > ONE_PASS_BITS  # the library's kOnePassBits
     b = {}
     b["k_prep"] = 4 * E + 4 * N                                         # src, labels
     if two:

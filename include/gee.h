@@ -156,7 +156,7 @@ int gee_graph_cache_clear(void);
  * in launch order:
  *   0 workspace memset, 1 k_prep (label counts, checks, first-digit histograms per
  *   range), 2 k_offsets (first pass), 3 k_scatter first pass (graphs with more than
- *   2^11 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final
+ *   2^8 nodes), 4 k_count (final-digit histograms, row lengths), 5 k_offsets (final
  *   pass), 6 k_scatter final pass (writes the CSR), 7 k_rowscan (index_pointers,
  *   unweighted degrees, hub-row list and chunks), 8 k_wdeg (weighted degrees, hub
  *   chunks then light rows), 9 k_spmm (Z with the fused epilogue, hub chunks then
@@ -219,8 +219,8 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
  *   Limit       returns GEE_ERR_TOO_LARGE, launching nothing, when
  *               gee_workspace_size(E, N, K, d_w != NULL, opts) exceeds
  *               GEE_STATIC_WORKSPACE_BYTES (about 4 million weighted directed edges on a
- *               graph with more than 2048 nodes, about 6.6 million with at most 2048,
- *               about twice that unweighted), and beyond gee_embed's own limits.
+ *               graph with more than 256 nodes, about 8 million with at most 256, about
+ *               twice that unweighted), and beyond gee_embed's own limits.
  *   Allocation  none: no cudaMalloc, cudaFree or allocating library call.
  *   Set-up      the first call on each device looks up the array's device address
  *               (cudaGetSymbolAddress) with that device current; make that first call

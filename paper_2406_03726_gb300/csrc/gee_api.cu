@@ -114,7 +114,7 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
     d.K = s.K;
     d.flags = o.flags & GEE_ALL_OPTIONS;
     d.nbits = std::max(1, bitlen(s.N > 0 ? (uint32_t)(s.N - 1) : 0u));
-    if (d.nbits <= kMaxDigitBits) {
+    if (d.nbits <= kOnePassBits) {
         d.npass = 1;
         d.lbits = 0;
         d.fbits = d.nbits;

@@ -21,6 +21,7 @@ constexpr int kPrepTile = 8192;                // edges (or nodes) per histogram
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;   // 2048 nodes per index-pointer tile
 constexpr int kMaxDigitBits = 11;
+constexpr int kOnePassBits = 8;                 // graphs with ids of at most this many bits take one pass
 constexpr int kMaxDigits = 1 << kMaxDigitBits;     // 2048 buckets per radix pass
 constexpr int kMaxK = 64;
 constexpr int kRegK = 8;                       // K <= 8: per-lane register accumulators
@@ -44,7 +45,7 @@ struct GraphDesc {
     uint32_t flags;
     // plan
     int32_t nbits;           // bits of a node id (>= 1)
-    int32_t npass;           // radix passes: 1 (nbits <= 11) or 2
+    int32_t npass;           // radix passes: 1 (nbits <= kOnePassBits) or 2
     int32_t lbits;           // digit bits of the first pass (2-pass graphs)
     int32_t fbits;           // digit bits of the final pass
     int32_t hub_C;           // rows longer than this are split into chunks of hub_C

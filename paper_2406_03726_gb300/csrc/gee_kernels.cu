@@ -6,7 +6,7 @@
 //   k_scatter  one stable LSD radix pass over the edges, keyed by source id, one CTA per
 //              range with TMA-staged tiles; the final pass writes the CSR (col_indices,
 //              data)
-//   k_count    (graphs with more than 2^11 nodes) final-digit histograms of the packed
+//   k_count    (graphs with more than 2^8 nodes) final-digit histograms of the packed
 //              first-pass output and the row lengths
 //   k_rowscan  index_pointers from the last pass's bucket offsets and the row lengths;
 //              unweighted degrees D_ii and the node table s_j = D_jj^-1/2 / n_{y_j};
@@ -193,7 +193,7 @@ __device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_c
 // input order).  A graph's edges are cut into ranges of range_tiles x 4096 edges.
 //
 //   k_prep       per range: histogram of the first-pass digit of the source ids
-//                (low lbits for 2-pass graphs, the whole id for graphs with <= 2^11
+//                (low lbits for 2-pass graphs, the whole id for graphs with <= 2^8
 //                nodes); per node tile: class sizes n_k and label checks
 //   k_offsets    per digit: exclusive prefix over (digit, range) -> the bucket offset
 //                at which each range starts writing each digit
