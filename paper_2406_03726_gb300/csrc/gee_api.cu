@@ -134,7 +134,11 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
     // rows longer than hub_C are split across CTAs: 64 vector loads per lane of the group
     d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
     d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
-    d.tiles_n = (int32_t)(((int64_t)s.N + kScanTile - 1) / kScanTile);
+    // index-pointer tiles: whole final-digit groups of 2^lbits rows, at least 256 rows,
+    // and no smaller than needed for about four tiles per SM over the launch's rows
+    d.scan_tile = std::max(kThreads, d.npass == 2 ? (1 << d.lbits) : 1);
+    while (d.scan_tile < kScanTile && rows_in_launch > (int64_t)4 * kSMs * d.scan_tile) d.scan_tile <<= 1;
+    d.tiles_n = (int32_t)(((int64_t)s.N + d.scan_tile - 1) / d.scan_tile);
     // rows a warp claims at once: blocks of up to 32 rows sorted by length, small enough
     // that a launch of few rows still gives every resident warp two blocks (a row's lanes
     // come from its length, so short rows share a warp in any block)

@@ -19,7 +19,7 @@ constexpr int kSortItems = 8;                  // keys per thread in a sort pass
 constexpr int kSortTile = kThreads * kSortItems;   // 2048 edges per sort tile
 constexpr int kPrepTile = 8192;                // edges (or nodes) per histogram tile
 constexpr int kScanItems = 8;
-constexpr int kScanTile = kThreads * kScanItems;   // 2048 nodes per index-pointer tile
+constexpr int kScanTile = kThreads * kScanItems;   // at most 2048 nodes per index-pointer tile
 constexpr int kMaxDigitBits = 11;
 constexpr int kOnePassBits = 8;                 // graphs with ids of at most this many bits take one pass
 constexpr int kMaxDigits = 1 << kMaxDigitBits;     // 2048 buckets per radix pass
@@ -51,7 +51,8 @@ struct GraphDesc {
     int32_t hub_C;           // rows longer than this are split into chunks of hub_C
     int32_t lpr_log2;        // log2(lanes cooperating on one light row)
     int32_t tiles_e;         // ceil(E / kSortTile)
-    int32_t tiles_n;         // ceil(N / kScanTile)
+    int32_t tiles_n;         // ceil(N / scan_tile)
+    int32_t scan_tile;       // rows per k_rowscan tile: 256..2048, whole final-digit groups
     int32_t rows_per_item;   // light rows per SpMM work item
     int32_t wdeg;            // 1: degrees and node table come from k_wdeg (weighted + Laplacian)
     int32_t range_tiles;     // sort tiles per range; one CTA scatters one range

@@ -893,8 +893,8 @@ __device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float 
 // of one final-pass digit hi are the 2^lbits consecutive ids (hi << lbits) | lo, in
 // order, so a row starts at the bucket base of hi (range 0's offset of digit hi) plus
 // the row lengths of the rows before it in that group.  1-pass graphs take the base
-// directly (there the digit is the row).  Tiles of 2048 rows hold whole groups, so no
-// tile depends on another.  Also: the hub list, and the node table when no weighted
+// directly (there the digit is the row).  Tiles of 256 to 2048 rows hold whole groups,
+// so no tile depends on another.  Also: the hub list, and the node table when no weighted
 // degree is needed.
 
 // Chunk offsets of the hub rows (prefix over their chunk counts), by one CTA.
@@ -931,22 +931,26 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     const int tid = threadIdx.x;
     if (tid == 0) s_err = 0;
     const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
-    const int64_t n0 = (int64_t)t * kScanTile;
-    const int n = (int)min64(kScanTile, (int64_t)sg.N - n0);
+    const int tile = sg.scan_tile, ipt = tile / kThreads;  // 1, 2, 4 or 8 rows per thread
+    const int64_t n0 = (int64_t)t * tile;
+    const int n = (int)min64(tile, (int64_t)sg.N - n0);
     auto pad = [](int i) { return i + (i >> 5); };
-    for (int i = tid; i < kScanTile; i += kThreads) buf[pad(i)] = (i < n) ? __ldcg(sg.rowcnt + n0 + i) : 0;
+    for (int i = tid; i < tile; i += kThreads) buf[pad(i)] = (i < n) ? __ldcg(sg.rowcnt + n0 + i) : 0;
     __syncthreads();
     uint32_t loc = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) loc += (uint32_t)buf[pad(tid * kScanItems + j)];
+    for (int j = 0; j < kScanItems; ++j)
+        if (j < ipt) loc += (uint32_t)buf[pad(tid * ipt + j)];
     uint32_t tot;
     uint32_t run = block_excl_scan(loc, s_scan, tot);
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const int i = pad(tid * kScanItems + j);
-        const uint32_t cnt = (uint32_t)buf[i];
-        buf[i] = (int32_t)run;
-        run += cnt;
+        if (j < ipt) {
+            const int i = pad(tid * ipt + j);
+            const uint32_t cnt = (uint32_t)buf[i];
+            buf[i] = (int32_t)run;
+            run += cnt;
+        }
     }
     __syncthreads();
     uint32_t err = 0;
@@ -972,7 +976,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
         if (i >= n) continue;
         const int64_t j = n0 + i;
         const uint32_t ex = (uint32_t)buf[pad(i)];
-        const int32_t cnt = (int32_t)((i + 1 < kScanTile ? (uint32_t)buf[pad(i + 1)] : tot) - ex);
+        const int32_t cnt = (int32_t)((i + 1 < tile ? (uint32_t)buf[pad(i + 1)] : tot) - ex);
         const int32_t start = (int32_t)(base[k] + ex - (uint32_t)buf[pad(i & ~gmask)]);
         sg.rowptr[j] = start;
         if (i == n - 1 && n0 + n == sg.N) sg.rowptr[sg.N] = start + cnt;
