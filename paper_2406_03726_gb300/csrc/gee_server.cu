@@ -86,7 +86,6 @@ class Pool {
     }
     size_t used() const { return used_; }
     size_t peak() const { return peak_; }
-    size_t size() const { return size_; }
 
   private:
     char *base_ = nullptr;
