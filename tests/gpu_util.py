@@ -21,6 +21,18 @@ def z_errors(Zg, Zo):
     return float(rel.max(initial=0.0)), bad_zero
 
 
+def z_error_report(Zg, Zo, what):
+    """One line with the max and 99th-percentile relative error over the non-zero oracle
+    entries (shown by pytest -s)."""
+    Zg = np.asarray(Zg, np.float64)
+    nz = Zo != 0
+    rel = np.abs(Zg[nz] - Zo[nz]) / np.abs(Zo[nz]) if nz.any() else np.zeros(1)
+    line = (f"parity {what}: max relative error {rel.max(initial=0.0):.2e}, "
+            f"p99 {np.percentile(rel, 99):.2e}, over {int(nz.sum())} non-zero entries")
+    print(line)
+    return line
+
+
 def assert_z_matches(Zg, Zo, rtol=RTOL, what=""):
     err, bad = z_errors(Zg, Zo)
     assert bad == 0, f"{what}: {bad} entries non-zero where the oracle is zero"

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from synth import batch_graph, batch_specs, chung_lu, random_tiny, sbm
 
-from gpu_util import RTOL, assert_z_matches, dev_graph, z_errors
+from gpu_util import RTOL, assert_z_matches, dev_graph, z_error_report, z_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -85,7 +85,9 @@ def test_sbm_2000_options_off_and_all(gee):
     for f in (0, ALL):
         Zg, st = run(gee, g, f)
         assert st == 0
-        assert_z_matches(Zg, oracle.embed_graph(g, f), what=f"sbm2000 flags {f}")
+        Zo = oracle.embed_graph(g, f)
+        assert_z_matches(Zg, Zo, what=f"sbm2000 flags {f}")
+        z_error_report(Zg, Zo, f"SBM N=2,000 flags {f}")
     src, dst, w, y = dev_graph(g)
     rowptr, col, _, nk, deg = gee.build_csr(src, dst, None, g.N, y, g.K, ALL)
     r_o, c_o, _ = oracle.csr(g.src, g.dst, None, g.N)
@@ -96,7 +98,9 @@ def test_sbm_10000_weighted_all_options(gee):
     g = sbm(10_000, seed=2, weighted=True)
     Zg, st = run(gee, g, ALL)
     assert st == 0
-    assert_z_matches(Zg, oracle.embed_graph(g, ALL), what="sbm10000")
+    Zo = oracle.embed_graph(g, ALL)
+    assert_z_matches(Zg, Zo, what="sbm10000")
+    z_error_report(Zg, Zo, "SBM N=10,000 weighted, all options")
     src, dst, w, y = dev_graph(g)
     rowptr, col, val, _, _ = gee.build_csr(src, dst, w, g.N, y, g.K, ALL)
     r_o, c_o, v_o = oracle.csr(g.src, g.dst, g.w, g.N)
@@ -114,7 +118,9 @@ def test_chung_lu_600k_all_options(gee, cl600k):
     g = cl600k
     Zg, st = run(gee, g, ALL)
     assert st == 0
-    assert_z_matches(Zg, oracle.embed_graph(g, ALL), what="chung-lu 600k")
+    Zo = oracle.embed_graph(g, ALL)
+    assert_z_matches(Zg, Zo, what="chung-lu 600k")
+    z_error_report(Zg, Zo, "Chung-Lu N=600,000, all options")
     r = np.linalg.norm(Zg, axis=1)
     assert np.all((np.abs(r - 1) < 1e-5) | (r == 0))
 
