@@ -66,7 +66,7 @@ def make_graph(name, rank=0):
     raise ValueError(name)
 
 
-# ---- algorithmic bytes per launch of each kernel ("Roofline") ------------
+# ---- algorithmic bytes per launch of each kernel ----------------------------------------
 
 def kernel_bytes(g):
     """Algorithmic DRAM bytes of one launch of each kernel: every array the kernel must
