@@ -80,3 +80,68 @@ def test_tuning_fields_checked_on_host(lib):
     best = gee.make_opts(7)
     assert gee.gee_autotune(None, None, None, 10, 5, None, 3, None, None, None, 0, None, None) == 1  # no best
     assert gee.gee_autotune(None, None, None, 0, 1 << 22, 1, 3, None, 1, 1, 0, None, best) == 2     # N too large
+
+
+def _c_layout(tmp_path, body):
+    """Compile and run a C program including gee.h (plain C, no CUDA); returns its stdout."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "gee.h"\nint main(void) {\n'
+                   + body + "return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    return subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+
+
+def test_binding_structs_match_header(tmp_path):
+    import ctypes
+    import paper_2406_03726_gb300._native as nat
+    structs = {"gee_opts": nat.gee_opts, "gee_graph": nat.gee_graph, "gee_server_config": nat.gee_server_config,
+               "gee_request": nat.gee_request, "gee_server_stats": nat.gee_server_stats}
+    body = ""
+    for name, cls in structs.items():
+        body += f'printf("{name} size %zu\\n", sizeof({name}));\n'
+        for f, _ in cls._fields_:
+            body += f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));\n'
+    got = {}
+    for line in _c_layout(tmp_path, body).splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_python_constants_match_header(tmp_path):
+    import paper_2406_03726_gb300 as gee
+    pairs = {"GEE_DIAG_AUG": gee.DIAG_AUG, "GEE_LAPLACIAN": gee.LAPLACIAN, "GEE_CORRELATION": gee.CORRELATION,
+             "GEE_ALL_OPTIONS": gee.ALL_OPTIONS, "GEE_NO_GRAPH_CACHE": gee.NO_GRAPH_CACHE,
+             "GEE_STATUS_INDEX": gee.STATUS_INDEX, "GEE_STATUS_LABEL": gee.STATUS_LABEL,
+             "GEE_STATUS_WEIGHT": gee.STATUS_WEIGHT, "GEE_STATUS_TIMEOUT": gee.STATUS_TIMEOUT,
+             "GEE_ERR_NOMEM": gee.ERR_NOMEM, "GEE_PENDING": gee.PENDING, "GEE_ERR_STATE": gee.ERR_STATE,
+             "GEE_MAX_N": gee.MAX_N, "GEE_MAX_E": gee.MAX_E, "GEE_MAX_K": gee.MAX_K,
+             "GEE_NUM_PHASES": len(gee.PHASES)}
+    body = "".join(f'printf("{k} %lld\\n", (long long)({k}));\n' for k in pairs)
+    got = dict((k, int(v)) for k, v in (line.split() for line in _c_layout(tmp_path, body).splitlines()))
+    for k, v in pairs.items():
+        assert got[k] == v, k
+
+
+def test_kernel_constants_match_header(tmp_path):
+    # the kernels carry their own copies of the status bits, option bits and K limit
+    hdr = open(os.path.join(ROOT, "paper_2406_03726_gb300", "csrc", "gee_internal.cuh")).read()
+    consts = {m[0]: int(m[1]) for m in re.findall(r"\b(k\w+) = (\d+)u?\b", hdr)}
+    body = "".join(f'printf("{k} %lld\\n", (long long)({k}));\n' for k in
+                   ("GEE_STATUS_INDEX", "GEE_STATUS_LABEL", "GEE_STATUS_WEIGHT", "GEE_STATUS_TIMEOUT",
+                    "GEE_DIAG_AUG", "GEE_LAPLACIAN", "GEE_CORRELATION", "GEE_MAX_K"))
+    c = dict((k, int(v)) for k, v in (line.split() for line in _c_layout(tmp_path, body).splitlines()))
+    assert (consts["kStIndex"], consts["kStLabel"], consts["kStWeight"], consts["kStTimeout"]) == \
+        (c["GEE_STATUS_INDEX"], c["GEE_STATUS_LABEL"], c["GEE_STATUS_WEIGHT"], c["GEE_STATUS_TIMEOUT"])
+    assert (consts["kOptAug"], consts["kOptLap"], consts["kOptCor"]) == \
+        (c["GEE_DIAG_AUG"], c["GEE_LAPLACIAN"], c["GEE_CORRELATION"])
+    assert consts["kMaxK"] == c["GEE_MAX_K"]
