@@ -70,7 +70,10 @@ typedef enum gee_error {
 #define GEE_STATUS_INDEX 1u   /* an edge endpoint outside [0, N) */
 #define GEE_STATUS_LABEL 2u   /* a label outside [-1, K) */
 #define GEE_STATUS_WEIGHT 4u  /* a non-finite weight, or a negative one with GEE_LAPLACIAN */
-#define GEE_STATUS_TIMEOUT 8u /* a bounded inter-CTA wait gave up (should never happen) */
+#define GEE_STATUS_TIMEOUT 8u /* a bounded wait for an asynchronous copy gave up (should never happen) */
+#define GEE_STATUS_INTERNAL 16u /* an internal invariant failed: a scratch index out of range, a
+                                   capacity exceeded (should never happen; indicates a library bug
+                                   or a workspace overwritten during the call) */
 
 /* Options.  Zero-initialise and set `flags`; the tuning fields select the kernel
  * shapes (0 = automatic) and never change which value is computed, only the order of
@@ -146,6 +149,10 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
  * another thread is inside gee_embed.  Returns GEE_OK or GEE_ERR_CUDA. */
 int gee_graph_cache_clear(void);
 
+/* Number of argument sets the launch cache currently remembers (captured or seen once),
+ * and in *captured (may be NULL) how many of them hold an instantiated CUDA graph. */
+int gee_graph_cache_size(int *captured);
+
 /*
  * gee_embed_timed -- gee_embed with CUDA events recorded on `stream` between its launch
  * phases; waits for the stream and stores the device time of each phase, in
@@ -177,7 +184,9 @@ int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w
  *   d_val     device float32 [E]  data (1.0 for unweighted input), or NULL to skip
  *   d_nk      device int32 [K]    class sizes n_k, or NULL
  *   d_deg     device float32 [N]  D_ii (row sum, +1 with GEE_DIAG_AUG), or NULL
- * Integer outputs are exact; for unweighted input d_deg holds exact integers.
+ * Integer outputs are exact.  For unweighted input d_deg holds exact integers for every
+ * row with fewer than 2^24 entries (float32 represents every integer below 2^24); a
+ * longer row's degree is its exact count rounded to float32 (relative error < 6e-8).
  */
 int gee_build_csr(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                   const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_rowptr,
@@ -221,10 +230,13 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
  *               GEE_STATIC_WORKSPACE_BYTES (about 4 million weighted directed edges on a
  *               graph with more than 256 nodes, about 8 million with at most 256, about
  *               twice that unweighted), and beyond gee_embed's own limits.
- *   Allocation  none: no cudaMalloc, cudaFree or allocating library call.
- *   Set-up      the first call on each device looks up the array's device address
- *               (cudaGetSymbolAddress) with that device current; make that first call
- *               before any stream capture.
+ *   Allocation  none: no cudaMalloc, cudaFree or allocating library call.  The launch
+ *               cache of gee_embed is bypassed (GEE_NO_GRAPH_CACHE is always set), so
+ *               repeated calls never capture or instantiate a CUDA graph either.
+ *   Set-up      every call looks up the array's device address (cudaGetSymbolAddress)
+ *               with the calling thread's current device; the first call on a device can
+ *               load the library's device code there, so make it before any stream
+ *               capture.
  *   Sharing     all calls on a device use the same array, which keeps the last call's
  *               contents; each call clears what must start at zero itself.  Calls that
  *               overlap on the GPU (different streams, different host threads) race on

@@ -9,6 +9,9 @@ Two independent forms of the same definitions:
 * ``embed`` / ``csr`` / ``degrees`` / ``label_counts`` / ``class_counts`` call the plain C
   edge-list oracle in ``gee_oracle.c`` (Section 2 edge-list GEE, Section 3 CSR).
 * ``dense.embed_dense`` evaluates Table 1 literally with dense NumPy matrices (small N).
+* ``embed_rows`` is the same edge-list oracle restated row by row on several host threads
+  (``gee_oracle_rows.c``): it is the all-core CPU baseline, bit-identical to ``embed``
+  because each row's sums keep the edge-list order.
 
 Parity pinning: every function here is checked in ``tests/test_oracle.py`` against
 closed forms, invariants, a library stable sort, brute force on tiny inputs and the
@@ -21,7 +24,7 @@ import os
 
 import numpy as np
 
-from ._build import build_oracle, library_path
+from ._build import build_oracle, library_path, sources
 
 DIAG_AUG = 1
 LAPLACIAN = 2
@@ -40,8 +43,7 @@ def _load():
     global _lib
     if _lib is None:
         path = library_path()
-        src = os.path.join(os.path.dirname(__file__), "gee_oracle.c")
-        if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(src):
+        if not os.path.exists(path) or any(os.path.getmtime(path) < os.path.getmtime(s) for s in sources()):
             build_oracle()
         lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
@@ -58,6 +60,8 @@ def _load():
         lib.oracle_class_counts.restype = None
         lib.oracle_embed.argtypes = [P, P, P, i64, i32, P, i32, u32, P]
         lib.oracle_embed.restype = ctypes.c_int
+        lib.oracle_embed_rows.argtypes = [P, P, P, i64, i32, P, i32, u32, ctypes.c_int, P]
+        lib.oracle_embed_rows.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -123,3 +127,21 @@ def embed(src, dst, w, N, labels, K, flags=0) -> np.ndarray:
 
 def embed_graph(g, flags=0) -> np.ndarray:
     return embed(g.src, g.dst, g.w, g.N, g.labels, g.K, flags)
+
+
+def embed_rows(src, dst, w, N, labels, K, flags=0, threads=None) -> np.ndarray:
+    """Z of ``embed``, computed row-parallel on ``threads`` host threads (default: all
+    cores); bit-identical to ``embed``."""
+    src, dst, w, y = _i32(src), _i32(dst), _f32(w), _i32(labels)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    Z = np.zeros((N, K), np.float64)
+    err = _load().oracle_embed_rows(_ptr(src), _ptr(dst), _ptr(w), src.size, N, _ptr(y), K, flags,
+                                    int(threads), _ptr(Z))
+    if err:
+        raise ValueError(f"oracle: invalid input (error bits {err})")
+    return Z
+
+
+def embed_rows_graph(g, flags=0, threads=None) -> np.ndarray:
+    return embed_rows(g.src, g.dst, g.w, g.N, g.labels, g.K, flags, threads)

@@ -1,5 +1,6 @@
-"""Compile the C oracle into ``oracle/liboracle.so`` (plain gcc, no architecture flags,
-no fast-math, so the same IEEE double arithmetic runs on x86-64 and AArch64)."""
+"""Compile the C oracle (the plain single-threaded form and its row-parallel restatement)
+into ``oracle/liboracle.so`` (plain gcc, no architecture flags, no fast-math, no FMA
+contraction, so the same IEEE double arithmetic runs on x86-64 and AArch64)."""
 import os
 import subprocess
 
@@ -10,11 +11,18 @@ def library_path() -> str:
     return os.path.join(_HERE, "liboracle.so")
 
 
+SOURCES = ("gee_oracle.c", "gee_oracle_rows.c")
+
+
+def sources():
+    return [os.path.join(_HERE, f) for f in SOURCES]
+
+
 def build_oracle() -> str:
     out = library_path()
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-           "-o", tmp, os.path.join(_HERE, "gee_oracle.c"), "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-fno-fast-math", "-ffp-contract=off",
+           "-o", tmp] + sources() + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

@@ -32,6 +32,7 @@ from ._native import (  # noqa: F401
     gee_embed_host,
     gee_embed_static,
     gee_graph_cache_clear,
+    gee_graph_cache_size,
     gee_autotune,
     gee_autotune_workspace_size,
     gee_embed_timed,
@@ -54,6 +55,7 @@ STATUS_INDEX = 1
 STATUS_LABEL = 2
 STATUS_WEIGHT = 4
 STATUS_TIMEOUT = 8
+STATUS_INTERNAL = 16
 
 ERR_NOMEM = 6
 PENDING = 7

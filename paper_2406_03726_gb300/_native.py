@@ -53,6 +53,7 @@ _SIGNATURES = {
     "gee_class_counts": ([_P, _P, _I32, _P, _I32, _P, _P], ctypes.c_int),
     "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "gee_graph_cache_clear": ([], ctypes.c_int),
+    "gee_graph_cache_size": ([_P], ctypes.c_int),
     "gee_autotune_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
     "gee_autotune": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P, _P], ctypes.c_int),
     "gee_batch_workspace_size": ([_P, _I32, _P], _SZ),
@@ -201,6 +202,13 @@ def gee_autotune(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_byt
 
 def gee_graph_cache_clear() -> int:
     return lib().gee_graph_cache_clear()
+
+
+def gee_graph_cache_size():
+    """(remembered argument sets, of which captured as CUDA graphs)."""
+    cap = ctypes.c_int(0)
+    n = lib().gee_graph_cache_size(ctypes.byref(cap))
+    return n, cap.value
 
 
 def make_graphs(items):

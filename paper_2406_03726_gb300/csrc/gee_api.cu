@@ -465,7 +465,7 @@ struct EmbedKey {
         return device == b.device && src == b.src && dst == b.dst && w == b.w && labels == b.labels && Z == b.Z &&
                ws == b.ws && status == b.status && E == b.E && N == b.N && K == b.K && o.flags == b.o.flags &&
                o.hub_threshold == b.o.hub_threshold && o.lanes_per_row == b.o.lanes_per_row &&
-               ws_bytes == b.ws_bytes && timed == b.timed;
+               o.rows_per_item == b.o.rows_per_item && ws_bytes == b.ws_bytes && timed == b.timed;
     }
 };
 
@@ -783,6 +783,18 @@ int gee_graph_cache_clear(void) {
     if (have_dev) cudaSetDevice(cur);
     gee::g_cache->clear();
     return GEE_OK;
+}
+
+int gee_graph_cache_size(int *captured) {
+    std::lock_guard<std::mutex> lk(gee::g_cache_mu);
+    int n = 0, c = 0;
+    if (gee::g_cache)
+        for (const auto &e : *gee::g_cache) {
+            ++n;
+            if (e.exec) ++c;
+        }
+    if (captured) *captured = c;
+    return n;
 }
 
 int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,

@@ -28,10 +28,10 @@ constexpr int kRegK = 8;                       // K <= 8: per-lane register accu
 constexpr int kHistCopies = 8;                 // digit totals are spread over 8 copies: fewer
                                                // atomics on one address at the end of k_prep
 
-constexpr int kSpinLimit = 1 << 22;            // bounded waits: ~1 s, then GEE_STATUS_TIMEOUT
+constexpr int kSpinLimit = 1 << 22;            // bounded copy waits: ~1 s, then GEE_STATUS_TIMEOUT
 
 // status bits (must equal GEE_STATUS_* in gee.h)
-constexpr uint32_t kStIndex = 1u, kStLabel = 2u, kStWeight = 4u, kStTimeout = 8u;
+constexpr uint32_t kStIndex = 1u, kStLabel = 2u, kStWeight = 4u, kStTimeout = 8u, kStInternal = 16u;
 constexpr uint32_t kOptAug = 1u, kOptLap = 2u, kOptCor = 4u;
 
 struct GraphDesc {

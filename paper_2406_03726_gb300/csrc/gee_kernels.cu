@@ -18,7 +18,8 @@
 //              fused into the epilogue; hub rows are split across CTAs and merged with
 //              two-sum compensation by the last CTA to finish
 //
-// Every inter-CTA or copy wait is bounded (kSpinLimit) and records kStTimeout instead of hanging;
+// Every copy wait is bounded (kSpinLimit) and records kStTimeout instead of hanging; a failed
+// internal invariant records kStInternal;
 // every global index derived from data is range-checked, so bad input cannot make a
 // kernel touch memory outside its buffers.
 #include "gee_internal.cuh"
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
         for (int s = tid; s < n; s += kThreads) {
             const uint32_t pos = spos[s];
             if (pos >= E32) {
-                err |= kStTimeout;
+                err |= kStInternal;
                 continue;
             }
             outk[pos] = spay[s];
@@ -813,7 +814,7 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
                               [&](int v) {
                 uint32_t hi = (uint32_t)v >> nb;
                 if (hi >= (uint32_t)D2) {
-                    err |= kStTimeout;
+                    err |= kStInternal;
                     hi = 0;
                 }
                 atomicAdd(&hw[hi], 1u);
@@ -838,7 +839,7 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
             const uint32_t p = (uint32_t)(e0 + i);
             uint32_t hi = ld_stream(sg.tmpk + p) >> nb;
             if (hi >= (uint32_t)D2) {
-                err |= kStTimeout;
+                err |= kStInternal;
                 hi = 0;
             }
             int a = lof, b = lol + 1;
@@ -990,7 +991,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
                 he.nch = (cnt + sg.hub_C - 1) / sg.hub_C;
                 c.cb.hubs[h] = he;
             } else {
-                err |= kStTimeout;  // capacity is sized so this cannot happen
+                err |= kStInternal;  // capacity is sized so this cannot happen
             }
         }
         if (!sg.wdeg) write_node_known(sg, j, (float)cnt + aug, lap, yv[k], ny[k]);
@@ -1312,7 +1313,7 @@ __device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t 
             const int64_t e = b + (q >> 2) * step + (q & 3);
             if (e >= lo && e < hi) {
                 uint32_t j = (uint32_t)cc[q];
-                if (j >= N) { err |= kStTimeout; continue; }
+                if (j >= N) { err |= kStInternal; continue; }
                 const int2 t = __ldg(g.tab + j);
                 const float p = vv[q] * __int_as_float(t.y);
 #pragma unroll
@@ -1352,7 +1353,7 @@ __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t
             const int64_t e = b + (q >> 2) * step + (q & 3);
             if (e >= lo && e < hi) {
                 uint32_t j = (uint32_t)cc[q];
-                if (j >= N) { err |= kStTimeout; continue; }
+                if (j >= N) { err |= kStInternal; continue; }
                 const int2 t = __ldg(g.tab + j);
                 sacc[t.x * 32 + lane] += vv[q] * __int_as_float(t.y);
                 if (t.x < 32) tlo |= 1u << t.x;

@@ -1,13 +1,19 @@
 // Continuous-batching embedding server (host runtime, C ABI in include/gee.h).
 //
 // Requests (host edge lists) are admitted as device memory from one pool frees up:
-// each admitted request gets its inputs and Z in the pool and its inputs are copied on a
-// copy stream.  A worker thread keeps forming batches of admitted requests and launches
-// each batch through the batch path (gee_embed_batch) on the next of several compute
-// streams, so batches that are admitted while others run overlap on the device.  A
-// batch's workspace (which holds the CSR of its graphs) and each request's Z stay
-// resident until the request is released.  Latency is measured from submission to the
-// moment the stream passes the batch (a host function enqueued after it).
+// each admitted request gets its inputs and Z in the pool.  A copy thread moves the
+// inputs to the device on a copy stream (pinned inputs directly, pageable ones through a
+// ring of pinned staging buffers).  A worker thread keeps forming batches of copied
+// requests and launches each batch through the batch path (gee_embed_batch) on the next
+// of several compute streams, so batches that are admitted while others run overlap on
+// the device.  A batch's workspace (which holds the CSR of its graphs) and each request's
+// Z stay resident until the request is released.  Latency is measured from submission to
+// the moment the stream passes the batch (a host function enqueued after it).
+//
+// Locking: the request mutex guards the queues, the pool and the request states only.
+// No CUDA call that can block (a copy from pageable memory, a batch launch with its
+// descriptor upload) runs while it is held, so submit, poll and release never wait
+// behind a copy.
 #include "../../include/gee.h"
 
 #include <cuda_runtime.h>
@@ -96,6 +102,9 @@ class Pool {
 
 enum class RState { Queued, Admitted, Running, Done, Cancelled };
 
+constexpr size_t kStageSlotBytes = 16u << 20;  // pinned staging for pageable inputs
+constexpr int kStageSlots = 4;
+
 struct Batch;
 
 struct Request {
@@ -123,6 +132,7 @@ struct Batch {
     int stream = 0;
     cudaEvent_t done = nullptr;
     std::atomic<bool> finished{false};
+    bool host_failed = false;  // the launch itself returned an error
     Clock::time_point t_done;
     int live = 0;  // requests not yet released
 };
@@ -149,14 +159,19 @@ struct gee_server {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;   // waiting for memory
-    std::deque<std::shared_ptr<Request>> ready;   // admitted, waiting for a launch
+    std::deque<std::shared_ptr<Request>> tocopy;  // admitted, inputs not copied yet
+    std::deque<std::shared_ptr<Request>> ready;   // copied (in stream order), waiting for a launch
     std::unordered_map<int64_t, std::shared_ptr<Request>> all;
     std::vector<std::shared_ptr<Batch>> inflight;
     int64_t next_ticket = 1;
     gee_server_stats stats{};
     bool stop = false;
-    std::thread worker;
+    std::thread worker, copier;
     int last_error = GEE_OK;
+    // pinned staging ring of the copy thread (pageable inputs), one event per slot
+    char *stage = nullptr;
+    cudaEvent_t stage_ev[kStageSlots] = {};
+    int stage_next = 0;
 };
 
 namespace {
@@ -171,7 +186,8 @@ void CUDART_CB on_batch_done(void *p) {
 // own fit in the pool (the own workspace guarantees every admitted request can run even
 // when the pool is fragmented).  Admission is strictly first-come first-served: a
 // request that does not fit yet stops admission, so later requests can never take the
-// memory an earlier one is waiting for.
+// memory an earlier one is waiting for.  Called with the mutex held: it only reserves
+// memory and hands the request to the copy thread.
 void admit(gee_server *s) {
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         auto r = *it;
@@ -194,32 +210,91 @@ void admit(gee_server *s) {
         r->d_w = r->in.w ? reinterpret_cast<float *>(take(sizeof(float) * (size_t)r->in.E)) : nullptr;
         r->d_y = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (size_t)r->in.N));
         r->d_Z = reinterpret_cast<float *>(take(sizeof(float) * (size_t)r->in.N * (size_t)r->in.K));
-        cudaStream_t cs = s->copy_stream;
-        if (r->in.E > 0) {
-            cudaMemcpyAsync(r->d_src, r->in.src, sizeof(int32_t) * (size_t)r->in.E, cudaMemcpyHostToDevice, cs);
-            cudaMemcpyAsync(r->d_dst, r->in.dst, sizeof(int32_t) * (size_t)r->in.E, cudaMemcpyHostToDevice, cs);
-            if (r->in.w)
-                cudaMemcpyAsync(r->d_w, r->in.w, sizeof(float) * (size_t)r->in.E, cudaMemcpyHostToDevice, cs);
-        }
-        if (r->in.N > 0)
-            cudaMemcpyAsync(r->d_y, r->in.labels, sizeof(int32_t) * (size_t)r->in.N, cudaMemcpyHostToDevice, cs);
-        cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming);
-        cudaEventRecord(r->copied, cs);
         r->state = RState::Admitted;
-        s->ready.push_back(r);
+        s->tocopy.push_back(r);
         it = s->queue.erase(it);
     }
     s->stats.queued = (int64_t)s->queue.size();
+}
+
+bool host_pinned(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Host -> device copy of n bytes on the copy stream: pinned sources directly, pageable
+// ones chunk by chunk through the staging ring (a slot is reused once the copy that last
+// read it has finished).  Runs on the copy thread without the mutex.
+int copy_in(gee_server *s, void *dst, const void *src, size_t n) {
+    if (n == 0) return GEE_OK;
+    cudaStream_t cs = s->copy_stream;
+    if (!s->stage || host_pinned(src))
+        return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, cs) == cudaSuccess ? GEE_OK : GEE_ERR_CUDA;
+    for (size_t off = 0; off < n; off += kStageSlotBytes) {
+        const size_t m = std::min(kStageSlotBytes, n - off);
+        const int k = s->stage_next;
+        s->stage_next = (k + 1) % kStageSlots;
+        if (cudaEventSynchronize(s->stage_ev[k]) != cudaSuccess) return GEE_ERR_CUDA;
+        char *slot = s->stage + (size_t)k * kStageSlotBytes;
+        std::memcpy(slot, static_cast<const char *>(src) + off, m);
+        if (cudaMemcpyAsync(static_cast<char *>(dst) + off, slot, m, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            return GEE_ERR_CUDA;
+        if (cudaEventRecord(s->stage_ev[k], cs) != cudaSuccess) return GEE_ERR_CUDA;
+    }
+    return GEE_OK;
+}
+
+// The copy thread: takes admitted requests in order, copies their inputs and passes them
+// on to the worker (ready) with an event that marks the end of their copies.
+void copier_loop(gee_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        if (s->tocopy.empty()) {
+            s->cv.wait_for(lk, std::chrono::microseconds(200));
+            continue;
+        }
+        auto r = s->tocopy.front();
+        s->tocopy.pop_front();
+        lk.unlock();
+        int rc = GEE_OK;
+        if (r->in.E > 0) {
+            rc = copy_in(s, r->d_src, r->in.src, sizeof(int32_t) * (size_t)r->in.E);
+            if (rc == GEE_OK) rc = copy_in(s, r->d_dst, r->in.dst, sizeof(int32_t) * (size_t)r->in.E);
+            if (rc == GEE_OK && r->in.w) rc = copy_in(s, r->d_w, r->in.w, sizeof(float) * (size_t)r->in.E);
+        }
+        if (rc == GEE_OK && r->in.N > 0)
+            rc = copy_in(s, r->d_y, r->in.labels, sizeof(int32_t) * (size_t)r->in.N);
+        if (rc == GEE_OK && cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming) != cudaSuccess)
+            rc = GEE_ERR_CUDA;
+        if (rc == GEE_OK && cudaEventRecord(r->copied, s->copy_stream) != cudaSuccess) rc = GEE_ERR_CUDA;
+        lk.lock();
+        if (rc != GEE_OK) s->last_error = rc;  // the request still runs; its batch reports
+        s->ready.push_back(r);
+        s->cv.notify_all();
+    }
 }
 
 gee_graph graph_of(const Request &r) {
     return gee_graph{r.d_src, r.d_dst, r.d_w, r.d_y, r.d_Z, r.in.E, r.in.N, r.in.K};
 }
 
-// Form one batch from admitted requests and launch it on a free compute stream: as many
-// ready requests (up to max_batch) as a fresh contiguous workspace can be found for;
-// failing that, the oldest ready request alone in its own workspace.
-bool launch_one(gee_server *s) {
+// Form one batch from copied requests and reserve it, with the mutex held: as many ready
+// requests (up to max_batch) as a fresh contiguous workspace can be found for; failing
+// that, the oldest ready request alone in its own workspace.  Returns null when nothing
+// can be launched now.  The caller launches the batch without the mutex (launch_batch).
+struct PendingLaunch {
+    std::shared_ptr<Batch> b;
+    std::vector<gee_graph> gs;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+bool reserve_batch(gee_server *s, PendingLaunch &pl) {
     if (s->ready.empty()) return false;
     int si = -1;
     for (int i = 0; i < (int)s->streams.size(); ++i)
@@ -255,11 +330,9 @@ bool launch_one(gee_server *s) {
     b->ws = own ? nullptr : ws;
     b->stream = si;
     b->d_status = reinterpret_cast<uint32_t *>(ws + ws_bytes - align_up(sizeof(uint32_t) * n));
-    cudaStream_t st = s->streams[si];
     for (size_t i = 0; i < n; ++i) {
         auto r = s->ready.front();
         s->ready.pop_front();
-        cudaStreamWaitEvent(st, r->copied, 0);
         r->state = RState::Running;
         r->batch = b;
         r->index_in_batch = (int)i;
@@ -270,16 +343,34 @@ bool launch_one(gee_server *s) {
         b->reqs.push_back(r);
     }
     b->live = (int)n;
-    const int rc = gee_embed_batch(gs.data(), (int32_t)n, &opts, ws, ws_bytes - align_up(sizeof(uint32_t) * n),
-                                   st, b->d_status);
-    if (rc != GEE_OK) s->last_error = rc;
-    cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
-    cudaEventRecord(b->done, st);
-    cudaLaunchHostFunc(st, on_batch_done, b.get());
     s->stream_busy[si] += 1;
-    s->inflight.push_back(b);
     s->stats.launches += 1;
+    pl.b = b;
+    pl.gs = std::move(gs);
+    pl.ws = ws;
+    pl.ws_bytes = ws_bytes;
     return true;
+}
+
+// Enqueue a reserved batch on its stream (no mutex held): wait for its inputs' copies,
+// run the batch path, then the completion event and host function.
+int launch_batch(gee_server *s, PendingLaunch &pl) {
+    Batch &b = *pl.b;
+    cudaStream_t st = s->streams[b.stream];
+    int rc = GEE_OK;
+    for (auto &r : b.reqs)
+        if (r->copied && cudaStreamWaitEvent(st, r->copied, 0) != cudaSuccess) rc = GEE_ERR_CUDA;
+    gee_opts opts;
+    std::memset(&opts, 0, sizeof(opts));
+    opts.flags = s->cfg.flags;
+    const size_t n = b.reqs.size();
+    if (rc == GEE_OK)
+        rc = gee_embed_batch(pl.gs.data(), (int32_t)n, &opts, pl.ws, pl.ws_bytes - align_up(sizeof(uint32_t) * n),
+                             st, b.d_status);
+    cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    cudaEventRecord(b.done, st);
+    cudaLaunchHostFunc(st, on_batch_done, pl.b.get());
+    return rc;
 }
 
 void reap(gee_server *s) {
@@ -298,6 +389,7 @@ void reap(gee_server *s) {
             b->t_done = Clock::now();
             s->last_error = GEE_ERR_CUDA;
         }
+        failed = failed || b->host_failed;
         for (auto &r : b->reqs) {
             r->latency_ms = std::chrono::duration<double, std::milli>(b->t_done - r->t_submit).count();
             r->failed = failed;
@@ -319,7 +411,19 @@ void worker_loop(gee_server *s) {
         reap(s);
         admit(s);
         bool launched = false;
-        while (launch_one(s)) launched = true;
+        PendingLaunch pl;
+        while (reserve_batch(s, pl)) {
+            launched = true;
+            lk.unlock();
+            const int rc = launch_batch(s, pl);
+            lk.lock();
+            if (rc != GEE_OK) {
+                s->last_error = rc;
+                pl.b->host_failed = true;
+            }
+            s->inflight.push_back(pl.b);
+            pl = PendingLaunch();
+        }
         s->stats.bytes_in_use = s->pool.used();
         s->stats.peak_bytes_in_use = s->pool.peak();
         s->cv.notify_all();
@@ -369,7 +473,21 @@ int gee_server_create(const gee_server_config *cfg, gee_server **out) {
     s->stream_busy.assign(s->cfg.streams, 0);
     for (auto &st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    // pinned staging for pageable inputs; without it such copies go straight from the
+    // pageable source (slower, still correct)
+    if (cudaHostAlloc(reinterpret_cast<void **>(&s->stage), kStageSlotBytes * kStageSlots, cudaHostAllocDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        s->stage = nullptr;
+    }
+    for (int k = 0; s->stage && k < kStageSlots; ++k)
+        if (cudaEventCreateWithFlags(&s->stage_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            for (int j = 0; j < k; ++j) cudaEventDestroy(s->stage_ev[j]);
+            cudaFreeHost(s->stage);
+            s->stage = nullptr;
+        }
     s->worker = std::thread(worker_loop, s);
+    s->copier = std::thread(copier_loop, s);
     *out = s;
     return GEE_OK;
 }
@@ -491,6 +609,7 @@ void gee_server_destroy(gee_server *s) {
         s->cv.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->copier.joinable()) s->copier.join();
     cudaDeviceSynchronize();
     for (auto &kv : s->all) {
         if (kv.second->copied) cudaEventDestroy(kv.second->copied);
@@ -499,6 +618,10 @@ void gee_server_destroy(gee_server *s) {
         if (b->done) cudaEventDestroy(b->done);
     for (auto &st : s->streams) cudaStreamDestroy(st);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->stage) {
+        for (int k = 0; k < kStageSlots; ++k) cudaEventDestroy(s->stage_ev[k]);
+        cudaFreeHost(s->stage);
+    }
     cudaFree(s->pool_mem);
     delete s;
 }

@@ -8,34 +8,26 @@
 // holds until the process exits -- and runs the ordinary gee_embed path on it.
 //
 // Host code cannot pass the array's name to a kernel (on the host the name is only a
-// stand-in, not a device address), so the device address is looked up once per device
-// with cudaGetSymbolAddress, on the first call made with that device current.
+// stand-in, not a device address), so every call looks up the device address with
+// cudaGetSymbolAddress for the current device.  The lookup allocates nothing and is not
+// cached: a cached address could go stale after the context of a device is torn down and
+// created again, and the kernels would then write through it.
 #include "../../include/gee.h"
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
+#include <cstring>
 
 namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[GEE_STATIC_WORKSPACE_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up once per device).
+// Device address of g_static_scratch on the current device.
 int static_scratch(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GEE_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return GEE_ERR_CUDA;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return GEE_ERR_CUDA;
+    *out = p;
     return GEE_OK;
 }
 
@@ -53,8 +45,14 @@ extern "C" int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, cons
         const int rc = static_scratch(&scratch);
         if (rc != GEE_OK) return rc;
     }
+    // The launch cache of gee_embed would capture and instantiate a CUDA graph on a repeated
+    // call, which can allocate: it is always bypassed here.
+    gee_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    o.flags |= GEE_NO_GRAPH_CACHE;
     // gee_embed clears the part of the scratch that must start at zero, on `stream`,
     // before its first kernel; whatever an earlier call left there does not matter.
-    return gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, opts, d_Z, scratch, GEE_STATIC_WORKSPACE_BYTES, stream,
+    return gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &o, d_Z, scratch, GEE_STATIC_WORKSPACE_BYTES, stream,
                      d_status);
 }

@@ -23,6 +23,8 @@ void oracle_class_counts(const int32_t *src, const int32_t *dst, int64_t E, int3
                          int32_t K, int64_t *C);
 int oracle_embed(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
                  const int32_t *y, int32_t K, uint32_t flags, double *Z);
+int oracle_embed_rows(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
+                      const int32_t *y, int32_t K, uint32_t flags, int threads, double *Z);
 
 static uint64_t rng_state;
 
@@ -67,6 +69,7 @@ static void run_case(int32_t N, int64_t E, int32_t K, int weighted) {
     double *deg = malloc(sizeof(double) * (size_t)(N + 1));
     int64_t *C = malloc(sizeof(int64_t) * (size_t)(N + 1) * (size_t)K);
     double *Z = malloc(sizeof(double) * (size_t)(N + 1) * (size_t)K);
+    double *Zr = malloc(sizeof(double) * (size_t)(N + 1) * (size_t)K);
 
     check(oracle_validate(src, dst, w, E, N, y, K, 7u) == 0, "valid input accepted", N, E, 7u);
     oracle_label_counts(y, N, K, nk);
@@ -83,6 +86,12 @@ static void run_case(int32_t N, int64_t E, int32_t K, int weighted) {
         oracle_degrees(src, w, E, N, flags, deg);
         for (int32_t i = 0; i < N; ++i) check(deg[i] >= 0.0 && isfinite(deg[i]), "finite degrees", N, E, flags);
         check(oracle_embed(src, dst, w, E, N, y, K, flags, Z) == 0, "embedding runs", N, E, flags);
+        for (int threads = 1; threads <= 5; threads += 2) {
+            check(oracle_embed_rows(src, dst, w, E, N, y, K, flags, threads, Zr) == 0, "row-parallel form runs",
+                  N, E, flags);
+            check(memcmp(Z, Zr, sizeof(double) * (size_t)N * (size_t)K) == 0,
+                  "row-parallel form is bit-identical", N, E, flags);
+        }
         for (int64_t q = 0; q < (int64_t)N * K; ++q) check(isfinite(Z[q]), "finite Z", N, E, flags);
         if (flags == 0 && !w)  /* Z n_k equals the class counts (Eq. 1 with one-hot W / n_k) */
             for (int64_t q = 0; q < (int64_t)N * K; ++q) {
@@ -103,10 +112,12 @@ static void run_case(int32_t N, int64_t E, int32_t K, int weighted) {
         int32_t keep = dst[0];
         dst[0] = N;
         check(oracle_embed(src, dst, w, E, N, y, K, 7u, Z) == 1, "index error reported", N, E, 7u);
+        check(oracle_embed_rows(src, dst, w, E, N, y, K, 7u, 3, Z) == 1, "row-parallel index error", N, E, 7u);
         dst[0] = keep;
         keep = y[0];
         y[0] = K;
         check(oracle_embed(src, dst, w, E, N, y, K, 7u, Z) == 2, "label error reported", N, E, 7u);
+        check(oracle_embed_rows(src, dst, w, E, N, y, K, 7u, 2, Z) == 2, "row-parallel label error", N, E, 7u);
         y[0] = keep;
         if (w) {
             float wk = w[0];
@@ -123,7 +134,7 @@ static void run_case(int32_t N, int64_t E, int32_t K, int weighted) {
     check(oracle_validate(src, dst, w, E, N, y, 0, 0u) == 8, "K < 1 rejected", N, E, 0u);
 
     free(src); free(dst); free(w); free(y); free(nk); free(rowptr); free(col); free(val);
-    free(deg); free(C); free(Z);
+    free(deg); free(C); free(Z); free(Zr);
 }
 
 int main(void) {

@@ -123,6 +123,7 @@ def test_python_constants_match_header(tmp_path):
              "GEE_ALL_OPTIONS": gee.ALL_OPTIONS, "GEE_NO_GRAPH_CACHE": gee.NO_GRAPH_CACHE,
              "GEE_STATUS_INDEX": gee.STATUS_INDEX, "GEE_STATUS_LABEL": gee.STATUS_LABEL,
              "GEE_STATUS_WEIGHT": gee.STATUS_WEIGHT, "GEE_STATUS_TIMEOUT": gee.STATUS_TIMEOUT,
+             "GEE_STATUS_INTERNAL": gee.STATUS_INTERNAL,
              "GEE_ERR_NOMEM": gee.ERR_NOMEM, "GEE_PENDING": gee.PENDING, "GEE_ERR_STATE": gee.ERR_STATE,
              "GEE_MAX_N": gee.MAX_N, "GEE_MAX_E": gee.MAX_E, "GEE_MAX_K": gee.MAX_K,
              "GEE_NUM_PHASES": len(gee.PHASES)}
@@ -138,10 +139,11 @@ def test_kernel_constants_match_header(tmp_path):
     consts = {m[0]: int(m[1]) for m in re.findall(r"\b(k\w+) = (\d+)u?\b", hdr)}
     body = "".join(f'printf("{k} %lld\\n", (long long)({k}));\n' for k in
                    ("GEE_STATUS_INDEX", "GEE_STATUS_LABEL", "GEE_STATUS_WEIGHT", "GEE_STATUS_TIMEOUT",
-                    "GEE_DIAG_AUG", "GEE_LAPLACIAN", "GEE_CORRELATION", "GEE_MAX_K"))
+                    "GEE_STATUS_INTERNAL", "GEE_DIAG_AUG", "GEE_LAPLACIAN", "GEE_CORRELATION", "GEE_MAX_K"))
     c = dict((k, int(v)) for k, v in (line.split() for line in _c_layout(tmp_path, body).splitlines()))
-    assert (consts["kStIndex"], consts["kStLabel"], consts["kStWeight"], consts["kStTimeout"]) == \
-        (c["GEE_STATUS_INDEX"], c["GEE_STATUS_LABEL"], c["GEE_STATUS_WEIGHT"], c["GEE_STATUS_TIMEOUT"])
+    assert (consts["kStIndex"], consts["kStLabel"], consts["kStWeight"], consts["kStTimeout"],
+            consts["kStInternal"]) == (c["GEE_STATUS_INDEX"], c["GEE_STATUS_LABEL"], c["GEE_STATUS_WEIGHT"],
+                                       c["GEE_STATUS_TIMEOUT"], c["GEE_STATUS_INTERNAL"])
     assert (consts["kOptAug"], consts["kOptLap"], consts["kOptCor"]) == \
         (c["GEE_DIAG_AUG"], c["GEE_LAPLACIAN"], c["GEE_CORRELATION"])
     assert consts["kMaxK"] == c["GEE_MAX_K"]

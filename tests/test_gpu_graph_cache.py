@@ -95,3 +95,28 @@ def test_timed_replay_reports_phases():
         assert np.array_equal(ph >= 0.0, ran), f"call {it}: phases {ph}"
     assert ran[gee.PHASES.index("k_scatter_final")] and ran[gee.PHASES.index("k_spmm")]
     assert gee.gee_graph_cache_clear() == 0
+
+
+def test_rows_per_item_is_part_of_the_cache_key():
+    # the same buffers with a different rows_per_item must run (and cache) a new launch
+    # plan, not replay the graph captured for the first value
+    import torch
+    import paper_2406_03726_gb300 as gee
+    g = chung_lu(30000, 200000, seed=36, K=12)
+    src, dst, w, y = dev_graph(g)
+    assert gee.gee_graph_cache_clear() == 0
+    n = max(gee.gee_workspace_size(g.E, g.N, g.K, False, gee.make_opts(gee.ALL_OPTIONS, 0, 0, r)) for r in (1, 8))
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    Z = {r: torch.empty((g.N, g.K), dtype=torch.float32, device="cuda") for r in (1, 8)}
+    for r in (1, 8):
+        opts = gee.make_opts(gee.ALL_OPTIONS, 0, 0, r)
+        for _ in range(3):  # seen, captured, replayed
+            rc = gee.gee_embed(src, dst, None, g.E, g.N, y, g.K, opts, Z[r], ws, n, None, None)
+            assert rc == 0, gee.gee_strerror(rc)
+    torch.cuda.synchronize()
+    assert gee.gee_graph_cache_size() == (2, 2)
+    # rows_per_item only groups rows into work items: the bits do not change
+    assert torch.equal(Z[1], Z[8])
+    assert_z_matches(Z[8].cpu().numpy(), oracle.embed_graph(g, gee.ALL_OPTIONS), what="rows_per_item 8")
+    assert gee.gee_graph_cache_clear() == 0
+    assert gee.gee_graph_cache_size() == (0, 0)

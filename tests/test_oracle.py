@@ -223,12 +223,20 @@ def test_correlation_rows_unit_or_zero(seed):
 def test_weight_scaling(seed):
     g = random_tiny(seed, weighted=True)
     w3 = (g.w * np.float32(3.0)).astype(np.float32)
-    for f in (0, 1):                       # without the Laplacian, Z is linear in w
-        Z = oracle.embed_graph(g, f)
-        Zs = oracle.embed(g.src, g.dst, w3, g.N, g.labels, g.K, f)
-        # augmentation adds an unscaled self term
-        if f == 0:
-            assert np.allclose(Zs, 3.0 * Z, rtol=1e-6, atol=0)
+    # without the Laplacian, A W is linear in w
+    Z = oracle.embed_graph(g, 0)
+    Zs = oracle.embed(g.src, g.dst, w3, g.N, g.labels, g.K, 0)
+    assert np.allclose(Zs, 3.0 * Z, rtol=1e-6, atol=0)
+    # augmentation adds the unscaled self term S = I W (S[i, y_i] = 1 / n_{y_i}), so
+    # Z(3w) = 3 (Z(w) - S) + S
+    nk = np.bincount(g.labels[g.labels >= 0], minlength=g.K).astype(np.float64)
+    S = np.zeros((g.N, g.K))
+    lab = np.nonzero(g.labels >= 0)[0]
+    S[lab, g.labels[lab]] = 1.0 / nk[g.labels[lab]]
+    Z = oracle.embed_graph(g, oracle.DIAG_AUG)
+    Zs = oracle.embed(g.src, g.dst, w3, g.N, g.labels, g.K, oracle.DIAG_AUG)
+    assert np.allclose(Zs, 3.0 * (Z - S) + S, rtol=1e-6, atol=1e-12)
+    assert not np.allclose(Zs, 3.0 * Z, rtol=1e-6, atol=1e-12) or not lab.size
     # with the Laplacian and no augmentation, Z does not depend on the scale of w
     Z = oracle.embed_graph(g, oracle.LAPLACIAN)
     Zs = oracle.embed(g.src, g.dst, w3, g.N, g.labels, g.K, oracle.LAPLACIAN)
@@ -285,3 +293,26 @@ def test_oracle_on_paper_sbm_small():
     Z1 = oracle.embed_graph(g, oracle.ALL_OPTIONS)
     Z2 = dense.embed_dense(g.src, g.dst, g.w, g.N, g.labels, g.K, oracle.ALL_OPTIONS)
     assert np.allclose(Z1, Z2, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_row_parallel_oracle_is_bit_identical(seed):
+    # the all-core CPU baseline restates the edge-list oracle row by row: each row's sums
+    # keep the edge-list order, so every bit of Z must agree, for any thread count
+    g = random_tiny(seed, n_max=80, e_max=600)
+    for f in ALL_FLAGS:
+        Z = oracle.embed_graph(g, f)
+        for threads in (1, 2, 7):
+            assert np.array_equal(oracle.embed_rows_graph(g, f, threads), Z)
+
+
+def test_row_parallel_oracle_larger_graphs_and_errors():
+    from synth import chung_lu
+    for g in (chung_lu(20000, 150000, seed=41, K=9, weighted=True), sbm(1200, seed=42)):
+        for f in (0, oracle.ALL_OPTIONS, oracle.DIAG_AUG | oracle.LAPLACIAN):
+            assert np.array_equal(oracle.embed_rows_graph(g, f, 6), oracle.embed_graph(g, f))
+    g = sbm(300, seed=43, weighted=True)
+    bad = g.dst.copy()
+    bad[5] = g.N
+    with pytest.raises(ValueError):
+        oracle.embed_rows(g.src, bad, g.w, g.N, g.labels, g.K, 7, 4)

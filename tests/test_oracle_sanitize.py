@@ -21,8 +21,8 @@ def test_oracle_under_asan_and_ubsan(tmp_path):
     exe = str(tmp_path / "oracle_sanitize")
     cmd = [gcc, "-std=c11", "-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
            "-fno-sanitize-recover=undefined", "-ffp-contract=off",
-           os.path.join(ROOT, "oracle", "gee_oracle.c"), os.path.join(HERE, "oracle_sanitize_driver.c"),
-           "-o", exe, "-lm"]
+           os.path.join(ROOT, "oracle", "gee_oracle.c"), os.path.join(ROOT, "oracle", "gee_oracle_rows.c"),
+           os.path.join(HERE, "oracle_sanitize_driver.c"), "-o", exe, "-pthread", "-lm"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         pytest.skip(f"no sanitizer build here: {r.stderr.strip()[:200]}")

@@ -5,7 +5,9 @@ latency-critical loop that must not call cudaMalloc) get a variant of gee_embed 
 scratch is an array built into the library instead of a caller workspace.  These tests
 call it through the C ABI and check its Z against gee_embed's on the same inputs, for
 two calls in a row on different graphs (so the second call runs on the scratch the first
-one left behind), and check that an oversized graph is refused without any launch.
+one left behind), check that repeated calls on the same buffers keep giving that Z while
+the device's free memory (cudaMemGetInfo) stays the same and no launch graph is cached,
+and check that an oversized graph is refused without any launch.
 
 This file is collected last on purpose: it is the only test that touches the library's
 built-in scratch array.
@@ -55,6 +57,33 @@ def test_static_scratch_matches_workspace_entry_point(gee):
         ref = _with_workspace(gee, g, flags)
         got = _static(gee, g, flags)
         assert_z_matches(got, ref, what=f"{g.name} flags {flags}")
+
+
+def test_static_repeated_calls_allocate_nothing(gee):
+    # the latency-loop case: the same buffers and options again and again
+    g = sbm(2000, seed=33, weighted=True)
+    src, dst, w, y = dev_graph(g)
+    ref = _with_workspace(gee, g, ALL)
+    Z = torch.empty((g.N, g.K), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    opts = gee.make_opts(ALL)
+    assert gee.gee_graph_cache_clear() == 0
+
+    def call():
+        Z.fill_(float("nan"))
+        rc = gee.gee_embed_static(src, dst, w, g.E, g.N, y, g.K, opts, Z, None, status)
+        assert rc == 0, gee.gee_strerror(rc)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert_z_matches(Z.cpu().double().numpy(), ref, what="static repeated call")  # no device copy
+
+    call()  # the first call on the device may load the library's device code
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(4):
+        call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+    assert gee.gee_graph_cache_size() == (0, 0)
 
 
 def test_static_scratch_refuses_oversized_graph(gee):
