@@ -5,14 +5,23 @@ label counts and checks, CSR build (radix sort by source), degrees and node tabl
 label-gather product with the fused epilogue.  Inputs are resident in HBM; L2 is flushed
 (256 MiB write) before every timed step, outside the timed interval.
 
-The timed steps call gee_embed, the public entry point (from its third call with the
-same arguments it replays a cached CUDA graph of its kernels).  Prints ONE JSON line
-(rank 0); `roofline` describes the dominant kernel, from per-kernel CUDA-event times of
-gee_embed_timed calls run right after the timed steps (events between kernels would add
-a few microseconds to every timed step), `hot_l2` times the same call back to back
-without the flush, and `cpu_baseline` times the FP64 oracle on this host.
+The headline workload is the largest single-graph configuration, the Chung-Lu graph of
+600,000 nodes and 10M undirected edges (K = 50).  The timed steps call gee_embed, the
+public entry point (from its third call with the same arguments it replays a cached CUDA
+graph of its kernels).  Prints ONE JSON line (rank 0):
+  roofline      the dominant kernel, from per-kernel CUDA-event times of gee_embed_timed
+                calls run right after the timed steps (events between kernels would add
+                a few microseconds to every timed step)
+  hot_l2        the same call back to back without the flush
+  e2e           the same metric through gee_embed_host (pinned host buffers, copies timed)
+  cpu_baseline  the FP64 oracle on this host: single thread, and row-parallel on all cores
+  configs       (one GPU, default run) the other workloads as sub-records: SBM N=10,000
+                (weighted), SBM N=2,000, the 4,096-graph batch (with the one-graph-per-
+                launch comparison) and the continuous-batching server (median of repeated
+                runs, with their spread)
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sbm10k|sbm2k|cl600k]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cl600k|sbm10k|sbm2k|batch|serve]
+                  [--no-sub] [--no-cpu-baseline]
   python bench.py --impl reference ...     (the oracle arm)
 """
 from __future__ import annotations
@@ -37,15 +46,20 @@ L2_FLUSH_BYTES = 256 << 20
 ONE_PASS_BITS = 8  # graphs with node ids of at most this many bits are sorted in one radix pass
 KERNEL_TIMING_STEPS = 50
 HOT_L2_STEPS = 50              # back-to-back calls without the flush, reported as hot_l2
+SUB_STEPS = 100                # timed steps of a single-graph sub-record
+SERVE_REPS = 5                 # repeated serving runs (median and spread reported)
+CPU_SINGLE_BUDGET_S = 10.0     # bounded CPU-baseline samples
+CPU_ALL_BUDGET_S = 5.0
 
 WORKLOADS = {
+    "cl600k": dict(desc="Chung-Lu N=600,000, 10M undirected edges (deduplicated, both directions stored), "
+                        "gamma 2.1, K=50 Zipf(1.2) classes, unweighted, all options (diag-aug + Laplacian + "
+                        "correlation), seed 3"),
     "sbm10k": dict(desc="SBM N=10,000, K=3, priors [0.2,0.3,0.5], p_in 0.13, p_out 0.10 "
                         "(~5.56M undirected edges, both directions stored), fp32 weights U(0,1], "
-                        "all options (diag-aug + Laplacian + correlation), seed 2"),
+                        "all options, seed 2"),
     "sbm2k": dict(desc="SBM N=2,000, K=3, priors [0.2,0.3,0.5], p_in 0.13, p_out 0.10, unweighted, "
                        "all options, seed 1"),
-    "cl600k": dict(desc="Chung-Lu N=600,000, 10M undirected edges (deduplicated), gamma 2.1, K=50 Zipf(1.2) "
-                        "classes, unweighted, all options, seed 3"),
     "batch": dict(desc="4,096 graphs in one launch sequence (CUDA graph): N log-uniform [100, 50,000], mean "
                        "degree U[5,200], SBM or Chung-Lu (gamma 2.1) per graph, K U{2..64}, weights U(0,1], "
                        "all options, seed 4"),
@@ -157,32 +171,74 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def time_oracle(g, budget_s=12.0, max_calls=1000):
+def cpu_model():
+    """CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle(g, threads=None, budget_s=CPU_SINGLE_BUDGET_S, max_calls=1000):
+    """Seconds per full-graph oracle call: the plain oracle (threads None) or its row-parallel
+    restatement on `threads` host threads (bit-identical results)."""
     import oracle
-    oracle.embed_graph(g, ALL_OPTIONS)  # warm (page-in, build)
+    call = (lambda: oracle.embed_graph(g, ALL_OPTIONS)) if threads is None else \
+        (lambda: oracle.embed_rows_graph(g, ALL_OPTIONS, threads))
+    call()  # warm (page-in, build)
     times = []
     t_end = time.perf_counter() + budget_s
     while len(times) < max_calls and (not times or time.perf_counter() < t_end):
         t0 = time.perf_counter()
-        oracle.embed_graph(g, ALL_OPTIONS)
+        call()
         times.append(time.perf_counter() - t0)
     return times
+
+
+def cpu_baseline(g):
+    """The FP64 oracle on this host, single thread and row-parallel on every core."""
+    nproc = os.cpu_count() or 1
+    t1 = time_oracle(g, None, CPU_SINGLE_BUDGET_S)
+    ta = time_oracle(g, nproc, CPU_ALL_BUDGET_S)
+    model = cpu_model()
+    one = g.E / (sum(t1) / len(t1))
+    allc = g.E / (sum(ta) / len(ta))
+    return {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(t1)} full-graph oracle calls ({g.E} directed edges each), {sum(t1):.1f} s, "
+                      "single thread",
+            "cpu_model": model, "nproc": nproc,
+            "all_cores": {"value": allc, "unit": UNIT, "cores": nproc, "kind": "oracle (row-parallel form, "
+                          "bit-identical)", "cpu_model": model,
+                          "sample": f"{len(ta)} full-graph calls on {nproc} threads, {sum(ta):.1f} s"}}
 
 
 # ---- arms -------------------------------------------------------------------------------
 
 def reference_arm(args):
+    """The oracle arm: the FP64 oracle on all host cores (its row-parallel form, bit-identical
+    to the plain one), one full-graph call per step."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return 0
     g = make_graph(args.workload)
     import oracle
+    nproc = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.embed_graph(g, ALL_OPTIONS)
+        oracle.embed_rows_graph(g, ALL_OPTIONS, nproc)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.embed_graph(g, ALL_OPTIONS)
+        oracle.embed_rows_graph(g, ALL_OPTIONS, nproc)
         times.append(time.perf_counter() - t0)
     mean = sum(times) / len(times)
     v = g.E / mean
@@ -190,8 +246,9 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "N": g.N, "E": g.E, "K": g.K},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"full graph per step ({g.E} directed edges), single thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle (row-parallel form)",
+                             "cpu_model": cpu_model(),
+                             "sample": f"full graph per step ({g.E} directed edges), {nproc} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -210,43 +267,40 @@ def batch_kernel_bytes(specs, graphs):
     return tot
 
 
-def batch_arm(args, ws_n, rank, local, dev):
+def measure_batch(gee, dev, n_graphs, steps, warmup, rank=0):
+    """The many-graph batch: `steps` CUDA-event-timed replays of one plan (CUDA graph), the
+    per-kernel roofline of one extra timed launch, and the plain one-graph-per-launch path
+    over the same graphs on the same stream.  Frees its device memory before returning."""
     import torch
-    import paper_2406_03726_gb300 as gee
     from synth import batch_specs
     from synth.torch_batch import batch_graph_torch
-    specs = batch_specs(args.batch_graphs, seed=4 + 1000 * rank)
+    specs = batch_specs(n_graphs, seed=4 + 1000 * rank)
     graphs = [batch_graph_torch(sp, dev) for sp in specs]
     torch.cuda.synchronize()
     E_tot = sum(sp["E"] for sp in specs)
     plan = gee.BatchPlan([(s, d, w, y, sp["N"], sp["K"]) for (s, d, w, y), sp in zip(graphs, specs)], ALL_OPTIONS)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         plan.launch(stream, use_graph=True)
     torch.cuda.synchronize()
     if int(plan.status.abs().sum().item()) != 0:
         raise RuntimeError("device status set")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if ws_n > 1:
-        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            plan.launch(stream, use_graph=True, status=False)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+    for i in range(steps):
+        ev[i][0].record(stream)
+        plan.launch(stream, use_graph=True, status=False)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    E_job = E_tot
-    if ws_n > 1:
-        total_ms, E_job = reduce_over_ranks(total_ms, E_tot, dev)
-    ms_per_step = total_ms / args.steps
+    ms_per_step = total_ms / steps
     # per-kernel times of one extra (timed) launch of the same plan
     phase = np.zeros(gee_phase_count(), np.float32)
     plan.launch_timed(phase, stream)
     names = gee.PHASES
     kb = batch_kernel_bytes(specs, graphs)
-    kernels = {names[i]: float(phase[i]) for i in range(len(names)) if phase[i] > 0 and names[i] in kb and kb[names[i]] > 0}
+    kernels = {names[i]: float(phase[i]) for i in range(len(names))
+               if phase[i] > 0 and names[i] in kb and kb[names[i]] > 0}
     dom = max(kernels, key=lambda k: kernels[k])
     peaks = load_peaks()
     per_kernel = {k: {"ms": round(v, 4), "alg_bytes": int(kb[k]), "gbs": round(kb[k] / (v * 1e-3) / 1e9, 1),
@@ -266,30 +320,110 @@ def batch_arm(args, ws_n, rank, local, dev):
         b.record(stream)
         torch.cuda.synchronize()
     solo_ms = a.elapsed_time(b)
+    launches = int(sum(1 for i, n in enumerate(names) if phase[i] >= 0 and n != "memset"))
+    out = {"value": E_tot / (ms_per_step * 1e-3), "unit": UNIT, "ms_per_step": ms_per_step, "steps": steps,
+           "workload": WORKLOADS["batch"]["desc"], "graphs": len(specs), "E": E_tot,
+           "N": sum(sp["N"] for sp in specs), "l2": "inputs (~40 GB) far larger than L2",
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                        "peak_source": peaks["source"], "traffic": traffic_for(dom, "batch"),
+                        "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel},
+           "one_graph_per_launch": {"value": E_tot / (solo_ms * 1e-3), "unit": UNIT, "ms": solo_ms},
+           "gpu_launches_per_step": launches}
+    plan.close()
+    del plan, graphs, wsb
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_arm(args, ws_n, rank, local, dev):
+    import torch
+    import paper_2406_03726_gb300 as gee
+    if ws_n > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        m = measure_batch(gee, dev, args.batch_graphs, args.steps, args.warmup, rank)
+    total_ms = m["ms_per_step"] * args.steps
+    E_job = m["E"]
+    if ws_n > 1:
+        total_ms, E_job = reduce_over_ranks(total_ms, m["E"], dev)
+    ms_per_step = total_ms / args.steps
     line = {"metric": METRIC, "value": E_job / (ms_per_step * 1e-3), "unit": UNIT, "n_gpus": ws_n,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch"]["desc"], "graphs": len(specs), "E": E_tot,
-                       "N": sum(sp["N"] for sp in specs), "l2": "inputs (~40 GB) far larger than L2",
+            "config": {"workload": m["workload"], "graphs": m["graphs"], "E": m["E"], "N": m["N"], "l2": m["l2"],
                        "parallelism": f"replicas x{ws_n} (independent batches, no collective)"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "peak_source": peaks["source"],
-                         "traffic": traffic_for(dom, "batch"), "alg_bytes_per_launch": int(kb[dom]),
-                         "kernels": per_kernel},
-            "one_graph_per_launch": {"value": E_tot / (solo_ms * 1e-3), "unit": UNIT, "ms": solo_ms},
+            "roofline": m["roofline"], "one_graph_per_launch": m["one_graph_per_launch"],
             "e2e": None, "e2e_note": "not measured for the batch (about 40 GB of host input)",
-            "gpu_launches": int(sum(1 for i, n in enumerate(names) if phase[i] >= 0 and n != "memset")) * args.steps,
-            "clocks": clk.summary()}
+            "gpu_launches": m["gpu_launches_per_step"] * args.steps, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line))
-    plan.close()
     return 0
 
 
-def serve_arm(args, ws_n, rank, local, dev):
+def _serve_once(gee, reqs, gaps):
+    """One serving run: requests `reqs` submitted at once (gaps None) or with the given
+    inter-arrival gaps in seconds; each request's latency runs from its submission to its
+    Z being ready."""
     import threading
+    srv = gee.Server(64 << 30, ALL_OPTIONS, max_batch=1024, streams=2)
+    tickets = [None] * len(reqs)
+
+    def submitter():
+        t_next = time.perf_counter()
+        for i, ((s_, d_, w_, y_), sp) in enumerate(reqs):
+            if gaps is not None:
+                t_next += gaps[i]
+                while True:
+                    dt = t_next - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(min(dt, 0.002))
+            tickets[i] = srv.submit(s_.numpy(), d_.numpy(), w_.numpy(), y_.numpy(), sp["N"], sp["K"])
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    lat = []
+    t_last = t_start
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0001)
+        res = srv.poll(tickets[i], wait=True)
+        if res is None:
+            raise RuntimeError("request did not complete")
+        lat.append(res[2])
+        t_last = time.perf_counter()
+        srv.release(tickets[i])
+    th.join()
+    st = srv.stats()
+    srv.close()
+    edges = sum(sp["E"] for _, sp in reqs)
+    span = t_last - t_start
+    lat = np.array(lat)
+    return {"requests": len(reqs), "edges": int(edges), "seconds": span, "edges_per_s": edges / span,
+            "req_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "launches": int(st["launches"]),
+            "peak_pool_bytes": int(st["peak_bytes_in_use"]), "pool_bytes": int(st["pool_bytes"])}
+
+
+def _median_spread(runs, keys=("edges_per_s", "p50_ms", "p99_ms", "req_per_s")):
+    out = {}
+    for k in keys:
+        v = [r[k] for r in runs]
+        out[k] = statistics.median(v)
+        out[k + "_min"] = min(v)
+        out[k + "_max"] = max(v)
+    out["runs"] = len(runs)
+    out["requests_per_run"] = runs[0]["requests"]
+    return out
+
+
+def measure_serving(gee, dev, R, reps, rank=0):
+    """The continuous-batching server: `reps` repetitions of (saturation, 50% and 90% of
+    that repetition's saturation rate), each of R requests; medians with min and max."""
     import torch
-    import paper_2406_03726_gb300 as gee
     from synth import batch_specs
     from synth.torch_batch import batch_graph_torch
     rng = np.random.default_rng(5 + 1000 * rank)
@@ -307,72 +441,203 @@ def serve_arm(args, ws_n, rank, local, dev):
     big_host = to_host(big)
     torch.cuda.empty_cache()
 
-    def draw(R):
-        return [big_host if rng.random() < 0.01 else pool[rng.integers(len(pool))] for _ in range(R)]
+    def draw(n):
+        return [big_host if rng.random() < 0.01 else pool[rng.integers(len(pool))] for _ in range(n)]
 
-    def run(reqs, rate):
-        srv = gee.Server(64 << 30, ALL_OPTIONS, max_batch=1024, streams=2)
-        tickets = [None] * len(reqs)
-        t_sub = [0.0] * len(reqs)
+    # one seeded trace per load level, replayed by every repetition: the spread over the
+    # repetitions is the system's, not the draw's
+    trace = draw(R)
+    unit_gaps = rng.exponential(1.0, R)           # Poisson arrivals at rate 1, scaled below
+    _serve_once(gee, draw(50), None)              # warm-up
+    sat = [_serve_once(gee, trace, None) for _ in range(reps)]
+    rate = statistics.median(r["req_per_s"] for r in sat)
+    r50 = [_serve_once(gee, trace, unit_gaps / (0.5 * rate)) for _ in range(reps)]
+    r90 = [_serve_once(gee, trace, unit_gaps / (0.9 * rate)) for _ in range(reps)]
+    torch.cuda.empty_cache()
+    return {"workload": WORKLOADS["serve"]["desc"], "saturation": _median_spread(sat),
+            "at_50pct": _median_spread(r50), "at_90pct": _median_spread(r90),
+            "trace": {"requests": R, "large_graphs": sum(1 for _, sp in trace if sp["N"] == big["N"]),
+                      "edges": int(sum(sp["E"] for _, sp in trace))},
+            "note": "median over repeated runs of one seeded trace, with min and max; the 50% and 90% "
+                    "arrival rates are fractions of the median saturation rate",
+            "h2d_bytes_per_request": int(sum(sp["E"] * 12 + sp["N"] * 4 for _, sp in trace) / R)}
 
-        def submitter():
-            t0 = time.perf_counter()
-            t_next = t0
-            for i, ((s_, d_, w_, y_), sp) in enumerate(reqs):
-                if rate:
-                    t_next += rng.exponential(1.0 / rate)
-                    while True:
-                        dt = t_next - time.perf_counter()
-                        if dt <= 0:
-                            break
-                        time.sleep(min(dt, 0.002))
-                t_sub[i] = time.perf_counter()
-                tickets[i] = srv.submit(s_.numpy(), d_.numpy(), w_.numpy(), y_.numpy(), sp["N"], sp["K"])
 
-        th = threading.Thread(target=submitter)
-        t_start = time.perf_counter()
-        th.start()
-        lat = []
-        t_last = t_start
-        for i in range(len(reqs)):
-            while tickets[i] is None:
-                time.sleep(0.0001)
-            res = srv.poll(tickets[i], wait=True)
-            if res is None:
-                raise RuntimeError("request did not complete")
-            lat.append(res[2])
-            t_last = time.perf_counter()
-            srv.release(tickets[i])
-        th.join()
-        st = srv.stats()
-        srv.close()
-        edges = sum(sp["E"] for _, sp in reqs)
-        span = t_last - t_start
-        lat = np.array(lat)
-        return {"requests": len(reqs), "edges": int(edges), "seconds": span, "edges_per_s": edges / span,
-                "req_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "launches": int(st["launches"]),
-                "peak_pool_bytes": int(st["peak_bytes_in_use"]), "pool_bytes": int(st["pool_bytes"])}
-
+def serve_arm(args, ws_n, rank, local, dev):
+    import paper_2406_03726_gb300 as gee
     R = max(200, args.steps)
-    run(draw(50), None)                                  # warm-up
     with ClockSampler(local) as clk:
-        sat = run(draw(R), None)                          # everything at once: saturation
-        r50 = run(draw(R), 0.5 * sat["req_per_s"])
-        r90 = run(draw(R), 0.9 * sat["req_per_s"])
+        m = measure_serving(gee, dev, R, SERVE_REPS, rank)
+    sat = m["saturation"]
     line = {"metric": METRIC, "value": sat["edges_per_s"] * ws_n, "unit": UNIT, "n_gpus": ws_n, "steps": R,
-            "warmup": 50, "ms_per_step": 1e3 * sat["seconds"] / R, "higher_is_better": True, "scaling": "weak",
+            "warmup": 50, "ms_per_step": 1e3 / sat["req_per_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serve"]["desc"], "requests_per_run": R,
+            "config": {"workload": m["workload"], "requests_per_run": R,
                        "parallelism": f"replicas x{ws_n} (independent servers, no collective)"},
-            "serving": {"saturation": sat, "at_50pct": r50, "at_90pct": r90},
-            "e2e": {"value": sat["edges_per_s"], "unit": UNIT,
-                    "h2d_bytes_per_step": int(sat["edges"] * 12 / R), "d2h_bytes_per_step": 0,
+            "serving": m,
+            "e2e": {"value": sat["edges_per_s"], "unit": UNIT, "h2d_bytes_per_step": m["h2d_bytes_per_request"],
+                    "d2h_bytes_per_step": 0,
                     "note": "host inputs in, Z resident on the device (the serving contract)"},
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line))
     return 0
+
+
+def measure_single(gee, g, dev, steps, warmup, workload, barrier=None):
+    """One graph: autotuned options, `steps` L2-flushed CUDA-event-timed gee_embed calls,
+    per-kernel times of gee_embed_timed calls right after, hot-L2 calls and the end-to-end
+    host-buffer path.  Returns the record (no cross-rank reduction)."""
+    import torch
+    E, N, K = g.E, g.N, g.K
+    t = lambda a: None if a is None else torch.from_numpy(a).to(dev)
+    src, dst, w, y = t(g.src), t(g.dst), t(g.w), t(g.labels)
+    # the project's autotuner picks the split threshold and rows per work item for this
+    # graph (outside the timed region; it times candidate calls itself)
+    opts, tune_ms = gee.autotune(src, dst, w, N, y, K, ALL_OPTIONS)
+    tuned = {"hub_threshold": int(opts.hub_threshold), "rows_per_item": int(opts.rows_per_item),
+             "autotune_ms_per_call": round(tune_ms, 4)}
+    for f in ("vec_width", "short_len"):
+        if hasattr(opts, f):
+            tuned[f] = int(getattr(opts, f))
+    nbytes = gee.gee_workspace_size(E, N, K, w is not None, opts)
+    wsb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    Z = torch.empty((N, K), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    phase = np.zeros(gee_phase_count(), np.float32)
+
+    def step_plain():
+        rc = gee.gee_embed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+
+    for _ in range(max(warmup, 3)):
+        step_plain()
+        # the timed call is the one the timed region repeats: its first call launches
+        # directly, the second captures its launch graph, later ones replay it
+        rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())}")
+
+    # ---- timed region: `steps` calls of the public entry point, each bracketed by CUDA
+    # events on the launch stream (from the third call on, gee_embed replays its graph)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    n_kt = min(steps, KERNEL_TIMING_STEPS)
+    phase_sum = np.zeros_like(phase)
+    phase_cnt = np.zeros_like(phase)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))               # L2 flush, outside the timed interval
+        ev[i][0].record(stream)
+        step_plain()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    # ---- kernel timing, right after: the same call with CUDA events between its kernels
+    # (gee_embed_timed), which the timed steps leave out because each event pair adds a
+    # few microseconds to the step
+    for i in range(n_kt):
+        flush.fill_(float(i))
+        rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+        ok = phase >= 0
+        phase_sum[ok] += phase[ok]
+        phase_cnt[ok] += 1
+    torch.cuda.synchronize()
+    # ---- hot-L2 steps: the same call without the flush, so a graph whose arrays fit in
+    # L2 is served from it (reported beside the flushed number, not as the value)
+    n_hot = min(steps, HOT_L2_STEPS)
+    ev_hot = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_hot)]
+    step_plain()
+    for i in range(n_hot):
+        ev_hot[i][0].record(stream)
+        step_plain()
+        ev_hot[i][1].record(stream)
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())}")
+    # ---- re-embedding with new labels on the CSR the last call built (gee_reembed), the
+    # iterative / predicted-labels use: L2-flushed calls with a permutation of the labels
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(9)
+    y2 = y[torch.randperm(N, generator=gen, device=dev)].contiguous()
+    Z2 = torch.empty_like(Z)
+    for _ in range(3):  # seen, captured, replayed
+        rc = gee.gee_reembed(y2, E, N, K, w is not None, opts, Z2, wsb, nbytes, stream, status)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+    n_re = min(steps, KERNEL_TIMING_STEPS)
+    ev_re = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_re)]
+    for i in range(n_re):
+        flush.fill_(float(i))
+        ev_re[i][0].record(stream)
+        gee.gee_reembed(y2, E, N, K, w is not None, opts, Z2, wsb, nbytes, stream, status)
+        ev_re[i][1].record(stream)
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} after gee_reembed")
+    re_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_re]))
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    hot_ms = float(np.median([a.elapsed_time(b) for a, b in ev_hot])) if n_hot else None
+    total_ms = sum(step_ms)
+    ms_per_step = total_ms / steps
+
+    # ---- per-kernel roofline of the dominant kernel
+    names = gee.PHASES
+    avg = {names[i]: float(phase_sum[i] / phase_cnt[i]) for i in range(len(names)) if phase_cnt[i] > 0}
+    kb = kernel_bytes(g)
+    kernels = {k: v for k, v in avg.items() if k in kb and kb[k] > 0}
+    dom = max(kernels, key=lambda k: kernels[k])
+    peaks = load_peaks()
+    achieved = kb[dom] / (kernels[dom] * 1e-3) / 1e9
+    per_kernel = {k: {"ms": round(float(v), 5), "alg_bytes": int(kb[k]),
+                      "gbs": round(kb[k] / (v * 1e-3) / 1e9, 1),
+                      "frac": round(kb[k] / (v * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)}
+                  for k, v in kernels.items()}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_source": peaks["source"], "traffic": traffic_for(dom, workload),
+                "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel,
+                "kernel_timing": f"CUDA events between the kernels of gee_embed_timed, {n_kt} L2-flushed "
+                                 "calls right after the timed steps, same process and clock sampling"}
+    # the whole step against the end-to-end algorithmic bytes (COO read once, CSR written
+    # once, then the product's bytes)
+    b_e2e = e2e_alg_bytes(g)
+    roofline["step"] = {"alg_bytes": int(b_e2e), "gbs": round(b_e2e / (ms_per_step * 1e-3) / 1e9, 1),
+                        "frac": round(b_e2e / (ms_per_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = e2e_measure(gee, g, dev, stream, opts, steps)
+    launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))  # per step
+    out = {"value": E / (ms_per_step * 1e-3), "unit": UNIT, "ms_per_step": ms_per_step, "steps": steps,
+           "total_ms": total_ms, "workload": WORKLOADS[workload]["desc"], "N": N, "E": E, "K": K,
+           "tuning": tuned, "roofline": roofline, "e2e": e2e, "gpu_launches_per_step": launches,
+           "l2": "flushed before every step (256 MiB write, untimed)"}
+    if hot_ms is not None:
+        out["hot_l2"] = {"ms_per_step": round(hot_ms, 5), "value": E / (hot_ms * 1e-3), "unit": UNIT,
+                         "steps": n_hot, "note": "median of back-to-back calls without the L2 flush"}
+    out["reembed"] = {"ms_per_call": round(re_ms, 5), "value": E / (re_ms * 1e-3), "unit": UNIT, "calls": n_re,
+                      "speedup_vs_embed": round(ms_per_step / re_ms, 2),
+                      "note": "gee_reembed with permuted labels on the CSR, degrees and plans of the last call "
+                              "(L2 flushed before each call)"}
+    del src, dst, w, y, y2, wsb, Z, Z2, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def e2e_alg_bytes(g):
+    """Algorithmic bytes of a whole step from the edge list: the COO read once, the CSR
+    written once, and the product's bytes."""
+    wt = 1 if g.w is not None else 0
+    return g.E * (8 + 4 * wt) + g.E * (4 + 4 * wt) + kernel_bytes(g)["k_spmm"]
 
 
 def gpu_arm(args):
@@ -391,132 +656,40 @@ def gpu_arm(args):
             torch.distributed.destroy_process_group()
         return rc
     g = make_graph(args.workload, rank)
-    E, N, K = g.E, g.N, g.K
-    t = lambda a: None if a is None else torch.from_numpy(a).to(dev)
-    src, dst, w, y = t(g.src), t(g.dst), t(g.w), t(g.labels)
-    # the project's autotuner picks the split threshold and rows per work item for this
-    # graph (outside the timed region; it times candidate calls itself)
-    opts, tune_ms = gee.autotune(src, dst, w, N, y, K, ALL_OPTIONS)
-    tuned = {"hub_threshold": int(opts.hub_threshold), "rows_per_item": int(opts.rows_per_item),
-             "autotune_ms_per_call": round(tune_ms, 4)}
-    nbytes = gee.gee_workspace_size(E, N, K, w is not None, opts)
-    wsb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    Z = torch.empty((N, K), dtype=torch.float32, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    phase = np.zeros(gee_phase_count(), np.float32)
-
-    def step_plain():
-        rc = gee.gee_embed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status)
-        if rc:
-            raise RuntimeError(gee.gee_strerror(rc))
-
-    for _ in range(max(args.warmup, 3)):
-        step_plain()
-        # the timed call is the one the timed region repeats: its first call launches
-        # directly, the second captures its launch graph, later ones replay it
-        rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
-        if rc:
-            raise RuntimeError(gee.gee_strerror(rc))
-    torch.cuda.synchronize()
-    if int(status.item()) != 0:
-        raise RuntimeError(f"device status {int(status.item())}")
-
-    # ---- timed region: K steps of the public call, each bracketed by CUDA events on the
-    # launch stream (from the third call on, gee_embed replays its cached launch graph)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    n_kt = min(args.steps, KERNEL_TIMING_STEPS)
-    phase_sum = np.zeros_like(phase)
-    phase_cnt = np.zeros_like(phase)
-    if ws_n > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    barrier = torch.distributed.barrier if ws_n > 1 else None
+    subs = {}
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(float(i))               # L2 flush, outside the timed interval
-            ev[i][0].record(stream)
-            step_plain()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        # ---- kernel timing, right after: the same call with CUDA events between its
-        # kernels (gee_embed_timed), which the timed steps leave out because each event
-        # pair adds a few microseconds to the step
-        for i in range(n_kt):
-            flush.fill_(float(i))
-            rc = gee.gee_embed_timed(src, dst, w, E, N, y, K, opts, Z, wsb, nbytes, stream, status, phase)
-            if rc:
-                raise RuntimeError(gee.gee_strerror(rc))
-            ok = phase >= 0
-            phase_sum[ok] += phase[ok]
-            phase_cnt[ok] += 1
-        torch.cuda.synchronize()
-        # ---- hot-L2 steps: the same call without the flush, so a graph whose arrays fit
-        # in L2 is served from it (reported beside the flushed number, not as the value)
-        n_hot = min(args.steps, HOT_L2_STEPS)
-        ev_hot = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(n_hot)]
-        step_plain()
-        for i in range(n_hot):
-            ev_hot[i][0].record(stream)
-            step_plain()
-            ev_hot[i][1].record(stream)
-        torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    hot_ms = float(np.median([a.elapsed_time(b) for a, b in ev_hot])) if n_hot else None
-    total_ms = sum(step_ms)
-    E_job = E
+        m = measure_single(gee, g, dev, args.steps, args.warmup, args.workload, barrier)
+        # the other workloads as sub-records (one GPU, default run)
+        if ws_n == 1 and not args.no_sub:
+            for name in ("sbm10k", "sbm2k"):
+                if name != args.workload:
+                    subs[name] = measure_single(gee, make_graph(name), dev, min(args.steps, SUB_STEPS),
+                                                args.warmup, name)
+            subs["batch"] = measure_batch(gee, dev, args.batch_graphs, 3, 3)
+            subs["serving"] = measure_serving(gee, dev, 200, SERVE_REPS)
+    total_ms, E_job = m["total_ms"], g.E
     if ws_n > 1:
-        total_ms, E_job = reduce_over_ranks(total_ms, E, dev)
+        total_ms, E_job = reduce_over_ranks(total_ms, g.E, dev)
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    if int(status.item()) != 0:
-        raise RuntimeError(f"device status {int(status.item())}")
     ms_per_step = total_ms / args.steps
     value = E_job / (ms_per_step * 1e-3)
-
-    # ---- per-kernel roofline of the dominant kernel
-    names = gee.PHASES
-    avg = {names[i]: float(phase_sum[i] / phase_cnt[i]) for i in range(len(names)) if phase_cnt[i] > 0}
-    kb = kernel_bytes(g)
-    kernels = {k: v for k, v in avg.items() if k in kb and kb[k] > 0}
-    dom = max(kernels, key=lambda k: kernels[k])
-    peaks = load_peaks()
-    achieved = kb[dom] / (kernels[dom] * 1e-3) / 1e9
-    per_kernel = {k: {"ms": round(float(v), 5), "alg_bytes": int(kb[k]),
-                      "gbs": round(kb[k] / (v * 1e-3) / 1e9, 1),
-                      "frac": round(kb[k] / (v * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)}
-                  for k, v in kernels.items()}
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "peak_source": peaks["source"], "traffic": traffic_for(dom, args.workload),
-                "alg_bytes_per_launch": int(kb[dom]), "kernels": per_kernel,
-                "kernel_timing": f"CUDA events between the kernels of gee_embed_timed, {n_kt} L2-flushed "
-                                 "calls right after the timed steps, same process and clock sampling"}
-
-    # ---- end to end through the host-buffer entry point (pinned memory)
-    e2e = e2e_measure(gee, g, dev, stream, opts, args)
-
-    launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))  # per step
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "N": N, "E": E, "K": K, "tuning": tuned,
-                       "l2": "flushed before every step (256 MiB write, untimed)",
+            "config": {"workload": m["workload"], "name": args.workload, "N": g.N, "E": g.E, "K": g.K,
+                       "tuning": m["tuning"], "l2": m["l2"],
                        "parallelism": f"replicas x{ws_n} (independent graphs, no collective)"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches * args.steps,
+            "roofline": m["roofline"], "e2e": m["e2e"], "gpu_launches": m["gpu_launches_per_step"] * args.steps,
             "clocks": clk.summary()}
-    if hot_ms is not None:
-        line["hot_l2"] = {"ms_per_step": round(hot_ms, 5), "value": E / (hot_ms * 1e-3), "unit": UNIT,
-                          "steps": n_hot, "note": "median of back-to-back calls without the L2 flush "
-                                                  "(this rank's own graph)"}
+    if "hot_l2" in m:
+        line["hot_l2"] = m["hot_l2"]
+    line["reembed"] = m["reembed"]
+    if subs:
+        line["configs"] = subs
     if rank == 0:
         if ws_n == 1 and not args.no_cpu_baseline:
-            times = time_oracle(g)
-            line["cpu_baseline"] = {"value": E / (sum(times) / len(times)), "unit": UNIT, "cores": 1,
-                                    "kind": "oracle",
-                                    "sample": f"{len(times)} full-graph oracle calls ({E} directed edges each), "
-                                              f"{sum(times):.1f} s, single thread"}
+            line["cpu_baseline"] = cpu_baseline(g)
         print(json.dumps(line))
     if ws_n > 1:
         torch.distributed.destroy_process_group()
@@ -527,7 +700,7 @@ def gee_phase_count():
     return 16  # room for the GEE_NUM_PHASES floats gee_embed_timed writes
 
 
-def e2e_measure(gee, g, dev, stream, opts, args):
+def e2e_measure(gee, g, dev, stream, opts, steps):
     import torch
     E, N, K = g.E, g.N, g.K
     n = gee.gee_host_workspace_size(E, N, K, g.w is not None, opts)
@@ -544,7 +717,7 @@ def e2e_measure(gee, g, dev, stream, opts, args):
 
     for _ in range(3):
         call()
-    steps = max(3, args.steps)
+    steps = max(3, min(steps, 100))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -586,8 +759,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gee", choices=["gee", "reference"])
-    ap.add_argument("--workload", default="sbm10k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cl600k", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the sub-records of the other workloads")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":

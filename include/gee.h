@@ -47,6 +47,14 @@ extern "C" {
 /* Not an option of the method: gee_embed launches its kernels one by one instead of
  * replaying a cached CUDA graph (see gee_embed). */
 #define GEE_NO_GRAPH_CACHE 0x100u
+/* Input format, not an option of the method: the edge list is undirected and lists each
+ * edge once.  Every listed edge (i, j, e) with i != j then adds e to both A_ij and A_ji (a
+ * self-loop (i, i, e) adds e to A_ii once), without the caller storing both directions:
+ * the reverse copies are made inside the CSR build, which reads the input arrays once per
+ * radix pass.  In the CSR, row i lists the edges with source i in input order, then the
+ * edges with target i (other than self-loops) in input order.  The CSR then holds up to 2E
+ * entries (gee_build_csr: col/val need room for 2E; rowptr[N] is the count). */
+#define GEE_SYMMETRIZE 0x200u
 
 /* Supported sizes. */
 #define GEE_MAX_N (1 << 21)
@@ -74,6 +82,8 @@ typedef enum gee_error {
 #define GEE_STATUS_INTERNAL 16u /* an internal invariant failed: a scratch index out of range, a
                                    capacity exceeded (should never happen; indicates a library bug
                                    or a workspace overwritten during the call) */
+#define GEE_STATUS_STALE 32u    /* gee_reembed: the workspace does not hold the CSR of a completed
+                                   gee_embed with the same sizes, options and workspace */
 
 /* Options.  Zero-initialise and set `flags`; the tuning fields select the kernel
  * shapes (0 = automatic) and never change which value is computed, only the order of
@@ -85,10 +95,18 @@ typedef struct gee_opts {
     int32_t lanes_per_row; /* graph-level lanes per light row (1,2,...,32; 0 = auto from the
                               mean degree): sets the automatic threshold (256 x lanes) */
     int32_t rows_per_item; /* light rows a warp claims at once: 1,2,4,...,32; 0 = auto */
+    int32_t vec_width;     /* 16-byte vectors of col (and data) each lane of the product kernel
+                              keeps in flight: 2, 4 or 8; 0 = auto (8, fewer if shared memory
+                              would hold less than two CTAs per SM).  Never changes the bits of
+                              Z (a lane's entries are added in the same order) */
+    int32_t short_len;     /* K > 8: light rows of at most this many entries are taken one lane
+                              per row, longer ones by a whole warp: 8, 16, 32, 64, 128 or 256;
+                              0 = auto (64).  Changes the order of additions of the rows between
+                              the old and the new bound */
 } gee_opts;
 
 /*
- * gee_autotune -- chooses hub_threshold and rows_per_item for one graph by running
+ * gee_autotune -- chooses the tuning fields of gee_opts for one graph by running
  * gee_embed with a small set of candidates around the automatic values and timing
  * each with CUDA events on `stream` (the call waits for the stream).  The fastest
  * candidate goes to *best (flags copied from opts->flags; a tuning field of opts that
@@ -103,6 +121,18 @@ size_t gee_autotune_workspace_size(int64_t E, int32_t N, int32_t K, int weighted
 int gee_autotune(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                  const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *d_workspace,
                  size_t workspace_bytes, void *stream, gee_opts *best, float *best_ms);
+
+/*
+ * The autotuner's choices persist across processes in a JSON file (one entry per line):
+ * gee_tune_cache_save writes every cached choice with the name of the GPU it was measured
+ * on; gee_tune_cache_load adds the file's entries measured on a GPU of the current
+ * device's name (*loaded = how many, may be NULL), so a later gee_autotune on such a GPU
+ * returns them without timing anything.  GEE_ERR_ARG for a missing or malformed file
+ * (then nothing is loaded).  gee_tune_cache_clear forgets every cached choice.
+ */
+int gee_tune_cache_save(const char *path);
+int gee_tune_cache_load(const char *path, int *loaded);
+int gee_tune_cache_clear(void);
 
 /* Bytes of device workspace gee_embed needs for a graph of this size.  `weighted` is
  * non-zero when a weight array will be passed.  opts may be NULL (defaults). */
@@ -144,6 +174,27 @@ size_t gee_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const g
 int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
               const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z,
               void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status);
+
+/*
+ * gee_reembed -- Z for NEW labels on a graph whose CSR is already built: the CSR of A,
+ * the degrees D and the split and bucket plans do not depend on the labels (Section 2: W
+ * is built from known or predicted labels, so an iterative or semi-supervised use embeds
+ * the same graph again and again with updated labels).  Only the class sizes n_k, the
+ * node table s_j = D_jj^-1/2 / n_{y_j} and the product with its epilogue run again.
+ *
+ *   d_labels      device int32 [N], the new y_j in [0, K) or -1.
+ *   E, N, K, weighted, opts, d_workspace, workspace_bytes
+ *                 exactly those of the last gee_embed (or gee_reembed) that used this
+ *                 workspace; its contents must be unchanged since.  K may not change.
+ *   d_Z, stream, d_status   as gee_embed.
+ * The result is bit-identical to gee_embed with the new labels (same plan, same sums).
+ * If the workspace does not hold such a build (checked on the device against a hash of
+ * the plan and the workspace address), GEE_STATUS_STALE is set in d_status and Z is
+ * undefined; every memory access still stays inside the buffers.  Repeated calls with the
+ * same arguments replay a cached CUDA graph, as gee_embed does.
+ */
+int gee_reembed(const int32_t *d_labels, int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts,
+                float *d_Z, void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status);
 
 /* Destroys the CUDA graphs cached by gee_embed (all devices).  Not to be called while
  * another thread is inside gee_embed.  Returns GEE_OK or GEE_ERR_CUDA. */
@@ -246,6 +297,43 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
 int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
                      const int32_t *d_labels, int32_t K, const gee_opts *opts, float *d_Z, void *stream,
                      uint32_t *d_status);
+
+/* ------------------------------------------------------------------------------------
+ * One graph split by source rows over several GPUs (one process per GPU).  Rows are
+ * independent once the node table {y_j, s_j = D_jj^-1/2 / n_{y_j}} of every node is known
+ * (Section 2: Z_i^k sums e_ij W_j^k over the row's own entries), so a rank that owns rows
+ * [r0, r1) needs only the edges whose source is in that range.  Per rank:
+ *   1. gee_shard_build   CSR of its rows and their degrees; its partial class sizes n_k
+ *   2. (caller)          all-reduce (sum) of n_k over the ranks
+ *   3. gee_shard_table   the node table entries of its rows, from the global n_k
+ *   4. (caller)          all-gather of the entries into the table of all N nodes
+ *   5. gee_shard_embed   Z of its rows, gathering the node table of any column
+ * The library does no communication; the caller moves K int32 (step 2) and 8 bytes per
+ * node (step 4), e.g. with NCCL.  All calls of one rank use the same arguments E, N, r0,
+ * r1, K, weighted, opts and workspace; steps 3 and 5 read what step 1 left in the
+ * workspace (step 5 checks it on the device, GEE_STATUS_STALE otherwise).  With the same
+ * explicit tuning fields the rows' sums run exactly as in gee_embed of the whole graph.
+ *
+ *   d_src, d_dst, d_w  device [E]: the rank's edges; every d_src[e] in [r0, r1), every
+ *                      d_dst[e] a global id in [0, N) (else GEE_STATUS_INDEX)
+ *   d_labels           device int32 [r1 - r0]: labels of the rank's rows
+ *   d_nk               device int32 [K]: out (build) the rank's class sizes; in (table) the
+ *                      sizes summed over all ranks
+ *   d_tab              device int32 [r1 - r0][2] (table, out: this rank's slice) or
+ *                      [N][2] (embed, in: the gathered table); entry j = {y_j, bits of s_j}
+ *   d_Z                device float32 [r1 - r0][K]: the rank's rows of Z
+ */
+size_t gee_shard_workspace_size(int64_t E, int32_t N, int32_t r0, int32_t r1, int32_t K, int weighted,
+                                const gee_opts *opts);
+int gee_shard_build(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N, int32_t r0,
+                    int32_t r1, const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_nk,
+                    void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status);
+int gee_shard_table(int64_t E, int32_t N, int32_t r0, int32_t r1, const int32_t *d_labels, int32_t K, int weighted,
+                    const gee_opts *opts, const int32_t *d_nk, int32_t *d_tab, void *d_workspace,
+                    size_t workspace_bytes, void *stream);
+int gee_shard_embed(int64_t E, int32_t N, int32_t r0, int32_t r1, const int32_t *d_labels, int32_t K, int weighted,
+                    const gee_opts *opts, const int32_t *d_tab, float *d_Z, void *d_workspace,
+                    size_t workspace_bytes, void *stream, uint32_t *d_status);
 
 /* ------------------------------------------------------------------------------------
  * Many graphs at once.  The graphs of a batch are embedded by the same kernels in one

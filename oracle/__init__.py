@@ -60,6 +60,8 @@ def _load():
         lib.oracle_class_counts.restype = None
         lib.oracle_embed.argtypes = [P, P, P, i64, i32, P, i32, u32, P]
         lib.oracle_embed.restype = ctypes.c_int
+        lib.oracle_symmetrize.argtypes = [P, P, P, i64, P, P, P]
+        lib.oracle_symmetrize.restype = i64
         lib.oracle_embed_rows.argtypes = [P, P, P, i64, i32, P, i32, u32, ctypes.c_int, P]
         lib.oracle_embed_rows.restype = ctypes.c_int
         _lib = lib
@@ -76,6 +78,17 @@ def _f32(a):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def symmetrize(src, dst, w=None):
+    """(src, dst, w) of the directed list of an undirected edge list given once per edge:
+    every edge in input order, then the reverse of every non-self-loop edge in input order."""
+    src, dst, w = _i32(src), _i32(dst), _f32(w)
+    E = src.size
+    os_, od = np.zeros(2 * E, np.int32), np.zeros(2 * E, np.int32)
+    ow = None if w is None else np.zeros(2 * E, np.float32)
+    n = _load().oracle_symmetrize(_ptr(src), _ptr(dst), _ptr(w), E, _ptr(os_), _ptr(od), _ptr(ow))
+    return os_[:n], od[:n], None if ow is None else ow[:n]
 
 
 def validate(src, dst, w, N, labels, K, flags=0) -> int:

@@ -64,6 +64,29 @@ int oracle_validate(const int32_t *src, const int32_t *dst, const float *w, int6
     return err;
 }
 
+/* An undirected edge list that lists each edge once, as the directed list of A: every
+ * edge (i, j, e) in input order, then for every edge with i != j the reverse (j, i, e),
+ * again in input order (a self-loop is one entry of A_ii).  out_* have room for 2E
+ * entries; returns the number written.  w and out_w may be NULL (unweighted). */
+int64_t oracle_symmetrize(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t *out_src,
+                          int32_t *out_dst, float *out_w) {
+    int64_t n = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        out_src[n] = src[e];
+        out_dst[n] = dst[e];
+        if (w && out_w) out_w[n] = w[e];
+        ++n;
+    }
+    for (int64_t e = 0; e < E; ++e) {
+        if (src[e] == dst[e]) continue;
+        out_src[n] = dst[e];
+        out_dst[n] = src[e];
+        if (w && out_w) out_w[n] = w[e];
+        ++n;
+    }
+    return n;
+}
+
 /* n_k = number of nodes j with y_j = k (Section 2, definition of W). */
 void oracle_label_counts(const int32_t *y, int32_t N, int32_t K, int64_t *nk) {
     for (int32_t k = 0; k < K; ++k) nk[k] = 0;

@@ -33,6 +33,14 @@ from ._native import (  # noqa: F401
     gee_embed_static,
     gee_graph_cache_clear,
     gee_graph_cache_size,
+    gee_reembed,
+    gee_tune_cache_clear,
+    gee_tune_cache_load,
+    gee_tune_cache_save,
+    gee_shard_build,
+    gee_shard_embed,
+    gee_shard_table,
+    gee_shard_workspace_size,
     gee_autotune,
     gee_autotune_workspace_size,
     gee_embed_timed,
@@ -50,12 +58,14 @@ LAPLACIAN = 2
 CORRELATION = 4
 ALL_OPTIONS = 7
 NO_GRAPH_CACHE = 0x100
+SYMMETRIZE = 0x200
 
 STATUS_INDEX = 1
 STATUS_LABEL = 2
 STATUS_WEIGHT = 4
 STATUS_TIMEOUT = 8
 STATUS_INTERNAL = 16
+STATUS_STALE = 32
 
 ERR_NOMEM = 6
 PENDING = 7
@@ -88,12 +98,13 @@ def workspace(E, N, K, weighted, opts=None, device=None):
 
 
 def embed(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row=0, ws=None, Z=None,
-          status=None, stream=None, rows_per_item=0):
+          status=None, stream=None, rows_per_item=0, vec_width=0, short_len=0, opts=None):
     """Z (float32 [N, K], on the device of ``src``) from device tensors.  ``status`` may be a
     uint32 device tensor of one element receiving the GEE_STATUS_* bits."""
     import torch
     E = int(src.numel())
-    opts = make_opts(flags, hub_threshold, lanes_per_row, rows_per_item)
+    if opts is None:
+        opts = make_opts(flags, hub_threshold, lanes_per_row, rows_per_item, vec_width, short_len)
     dev = labels.device
     if Z is None:
         Z = torch.empty((N, K), dtype=torch.float32, device=dev)
@@ -130,14 +141,18 @@ def build_csr(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row
     opts = make_opts(flags, hub_threshold, lanes_per_row)
     n = gee_workspace_size(E, N, K, w is not None, opts)
     ws = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    cap = 2 * E if flags & SYMMETRIZE else E      # both copies of every undirected edge
     rowptr = torch.empty(N + 1, dtype=torch.int32, device=dev)
-    col = torch.empty(E, dtype=torch.int32, device=dev)
-    val = torch.empty(E, dtype=torch.float32, device=dev)
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    val = torch.empty(cap, dtype=torch.float32, device=dev)
     nk = torch.empty(K, dtype=torch.int32, device=dev)
     deg = torch.empty(N, dtype=torch.float32, device=dev)
     rc = gee_build_csr(src, dst, w, E, N, labels, K, opts, rowptr, col, val, nk, deg, ws, ws.numel(), stream,
                        status)
     _check(rc, "gee_build_csr")
+    if flags & SYMMETRIZE:
+        used = int(rowptr[N].item())
+        col, val = col[:used], val[:used]
     return rowptr, col, val, nk, deg
 
 

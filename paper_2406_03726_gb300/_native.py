@@ -15,7 +15,8 @@ _I32, _I64, _U32, _SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.
 
 class gee_opts(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("hub_threshold", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("rows_per_item", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("rows_per_item", ctypes.c_int32),
+                ("vec_width", ctypes.c_int32), ("short_len", ctypes.c_int32)]
 
 
 class gee_graph(ctypes.Structure):
@@ -54,6 +55,15 @@ _SIGNATURES = {
     "gee_embed_static": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "gee_graph_cache_clear": ([], ctypes.c_int),
     "gee_graph_cache_size": ([_P], ctypes.c_int),
+    "gee_tune_cache_save": ([ctypes.c_char_p], ctypes.c_int),
+    "gee_tune_cache_load": ([ctypes.c_char_p, _P], ctypes.c_int),
+    "gee_tune_cache_clear": ([], ctypes.c_int),
+    "gee_reembed": ([_P, _I64, _I32, _I32, ctypes.c_int, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
+    "gee_shard_workspace_size": ([_I64, _I32, _I32, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_shard_build": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
+    "gee_shard_table": ([_I64, _I32, _I32, _I32, _P, _I32, ctypes.c_int, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+    "gee_shard_embed": ([_I64, _I32, _I32, _I32, _P, _I32, ctypes.c_int, _P, _P, _P, _P, _SZ, _P, _P],
+                        ctypes.c_int),
     "gee_autotune_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
     "gee_autotune": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P, _P], ctypes.c_int),
     "gee_batch_workspace_size": ([_P, _I32, _P], _SZ),
@@ -123,8 +133,8 @@ def stream_handle(stream):
     return stream.cuda_stream
 
 
-def make_opts(flags=0, hub_threshold=0, lanes_per_row=0, rows_per_item=0):
-    return gee_opts(flags, hub_threshold, lanes_per_row, rows_per_item)
+def make_opts(flags=0, hub_threshold=0, lanes_per_row=0, rows_per_item=0, vec_width=0, short_len=0):
+    return gee_opts(flags, hub_threshold, lanes_per_row, rows_per_item, vec_width, short_len)
 
 
 def _opts_ref(opts):
@@ -202,6 +212,47 @@ def gee_autotune(src, dst, w, E, N, labels, K, opts, Z, workspace, workspace_byt
 
 def gee_graph_cache_clear() -> int:
     return lib().gee_graph_cache_clear()
+
+
+def gee_reembed(labels, E, N, K, weighted, opts, Z, workspace, workspace_bytes, stream=None, d_status=None) -> int:
+    return lib().gee_reembed(ptr(labels), E, N, K, int(bool(weighted)), _opts_ref(opts), ptr(Z), ptr(workspace),
+                             workspace_bytes, stream_handle(stream), ptr(d_status))
+
+
+def gee_shard_workspace_size(E, N, r0, r1, K, weighted, opts=None) -> int:
+    return lib().gee_shard_workspace_size(E, N, r0, r1, K, int(bool(weighted)), _opts_ref(opts))
+
+
+def gee_shard_build(src, dst, w, E, N, r0, r1, labels, K, opts, nk, workspace, workspace_bytes, stream=None,
+                    d_status=None) -> int:
+    return lib().gee_shard_build(ptr(src), ptr(dst), ptr(w), E, N, r0, r1, ptr(labels), K, _opts_ref(opts), ptr(nk),
+                                 ptr(workspace), workspace_bytes, stream_handle(stream), ptr(d_status))
+
+
+def gee_shard_table(E, N, r0, r1, labels, K, weighted, opts, nk, tab, workspace, workspace_bytes, stream=None) -> int:
+    return lib().gee_shard_table(E, N, r0, r1, ptr(labels), K, int(bool(weighted)), _opts_ref(opts), ptr(nk), ptr(tab),
+                                 ptr(workspace), workspace_bytes, stream_handle(stream))
+
+
+def gee_shard_embed(E, N, r0, r1, labels, K, weighted, opts, tab, Z, workspace, workspace_bytes, stream=None,
+                    d_status=None) -> int:
+    return lib().gee_shard_embed(E, N, r0, r1, ptr(labels), K, int(bool(weighted)), _opts_ref(opts), ptr(tab), ptr(Z),
+                                 ptr(workspace), workspace_bytes, stream_handle(stream), ptr(d_status))
+
+
+def gee_tune_cache_save(path) -> int:
+    return lib().gee_tune_cache_save(str(path).encode())
+
+
+def gee_tune_cache_load(path):
+    """(rc, entries loaded)."""
+    n = ctypes.c_int(0)
+    rc = lib().gee_tune_cache_load(str(path).encode(), ctypes.byref(n))
+    return rc, n.value
+
+
+def gee_tune_cache_clear() -> int:
+    return lib().gee_tune_cache_clear()
 
 
 def gee_graph_cache_size():

@@ -13,7 +13,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <functional>
 #include <mutex>
 #include <vector>
@@ -27,12 +29,15 @@ size_t scatter_smem(int max_digit_bits);
 cudaError_t launch_count(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_rowscan(const Ctx &c, int blocks, cudaStream_t st);
 cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st);
-cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st);
+cudaError_t launch_spmm(const Ctx &c, int blocks, int kpad, int ring, cudaStream_t st);
 cudaError_t launch_class_counts(const int32_t *rowptr, const int32_t *col, int32_t N, const int32_t *y, int32_t K,
                                 int32_t *C, int blocks, cudaStream_t st);
 cudaError_t launch_fill(float *p, int64_t n, float v, cudaStream_t st);
+cudaError_t launch_relabel(const Ctx &c, cudaStream_t st);
+cudaError_t launch_nodetab(const Ctx &c, cudaStream_t st);
+cudaError_t launch_stamp_check(const Ctx &c, cudaStream_t st);
 cudaError_t configure_kernels();
-int occupancy_spmm(bool smem_acc);
+int occupancy_spmm(int kpad, int ring, bool ringw);
 int occupancy_wdeg();
 
 namespace {
@@ -45,7 +50,7 @@ constexpr int kWarpsPerSM = 24;             // resident warps of the row kernels
 struct DeviceInfo {
     bool ready = false;
     int sms = 0;
-    int occ_spmm[2] = {1, 1};  // CTAs per SM of k_spmm without / with shared-memory accumulators
+    int occ_spmm[3][8][2] = {};  // CTAs per SM of k_spmm by ring depth (2, 4, 8), classes / 8 - 1, val ring
     int occ_wdeg = 1;
 };
 
@@ -60,7 +65,9 @@ int device_info(DeviceInfo &out) {
     if (!d.ready) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEE_ERR_CUDA;
         if (configure_kernels() != cudaSuccess) return GEE_ERR_CUDA;
-        for (int i = 0; i < 2; ++i) d.occ_spmm[i] = occupancy_spmm(i == 1);
+        for (int v = 0; v < 3; ++v)
+            for (int i = 0; i < 8; ++i)
+                for (int w = 0; w < 2; ++w) d.occ_spmm[v][i][w] = occupancy_spmm(8 * (i + 1), 2 << v, w != 0);
         d.occ_wdeg = occupancy_wdeg();
         d.ready = true;
     }
@@ -101,6 +108,18 @@ struct Shape {
     bool weighted;
 };
 
+// Ranges of range_tiles sort tiles, one scatter CTA each.  Symmetrizing: as many ranges
+// over the input read forward as over the input read reversed (no range mixes the two).
+void set_ranges(GraphDesc &d, int32_t range_tiles) {
+    d.range_tiles = range_tiles;
+    if (d.sym) {
+        const int64_t half_tiles = (d.Ein + kSortTile - 1) / kSortTile;
+        d.ranges = 2 * (int32_t)((half_tiles + range_tiles - 1) / range_tiles);
+    } else {
+        d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
+    }
+}
+
 // Plan parameters of one graph.  Everything that decides the order of floating-point
 // additions depends only on the graph and the options (never on the batch it is part of,
 // so a graph gives the same bits alone and in a batch); the row-block size only groups
@@ -109,13 +128,18 @@ struct Shape {
 // the automatic row-block size keeps the launch's warps busy, not each graph's.
 void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d, int64_t rows_in_launch = -1) {
     if (rows_in_launch < 0) rows_in_launch = s.N;
-    d.E = s.E;
+    d.sym = (o.flags & GEE_SYMMETRIZE) ? 1 : 0;
+    d.Ein = s.E;
+    d.E = d.sym ? 2 * s.E : s.E;  // the CSR holds at most both copies of every input edge
     d.N = s.N;
     d.K = s.K;
     d.flags = o.flags & GEE_ALL_OPTIONS;
-    d.nbits = std::max(1, bitlen(s.N > 0 ? (uint32_t)(s.N - 1) : 0u));
-    if (d.nbits <= kOnePassBits) {
-        d.npass = 1;
+    d.nbits = std::max(d.sym ? 2 : 1, bitlen(s.N > 0 ? (uint32_t)(s.N - 1) : 0u));
+    d.ncols = s.N;      // a row shard overrides these three (plan_shard)
+    d.pbits = d.nbits;
+    d.row0 = 0;
+    if (d.nbits <= kOnePassBits && !d.sym) {  // symmetrizing always takes two passes (the
+        d.npass = 1;                           // first one marks the dropped self-loop copies)
         d.lbits = 0;
         d.fbits = d.nbits;
     } else {
@@ -123,7 +147,7 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
         d.lbits = (d.nbits + 1) / 2;
         d.fbits = d.nbits - d.lbits;
     }
-    const double mean = s.N > 0 ? (double)s.E / (double)s.N : 0.0;
+    const double mean = s.N > 0 ? (double)d.E / (double)s.N : 0.0;
     int lpr = o.lanes_per_row;
     if (lpr <= 0) {
         lpr = 1;
@@ -133,7 +157,7 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
     d.lpr_log2 = ilog2_pow2(lpr);
     // rows longer than hub_C are split across CTAs: 64 vector loads per lane of the group
     d.hub_C = o.hub_threshold > 0 ? o.hub_threshold : std::max(1024, 256 * lpr);
-    d.tiles_e = (int32_t)((s.E + kSortTile - 1) / kSortTile);
+    d.tiles_e = (int32_t)((d.E + kSortTile - 1) / kSortTile);
     // index-pointer tiles: whole final-digit groups of 2^lbits rows, at least 256 rows,
     // and no smaller than needed for about four tiles per SM over the launch's rows
     d.scan_tile = std::max(kThreads, d.npass == 2 ? (1 << d.lbits) : 1);
@@ -151,13 +175,34 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
         d.rows_per_item = rpi;
     }
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
+    d.short_len = o.short_len > 0 ? o.short_len : 64;
+    d.vec = o.vec_width;  // 0: chosen at launch from the shared memory it leaves
+    // K > 8: capacities of the length buckets.  Bucket b >= 1 of the one-lane buckets
+    // holds rows of more than lo_b entries (so at most E / (lo_b + 1) of them); the
+    // whole-warp bucket rows of more than short_len entries.
+    int64_t off = 0;
+    for (int b = 0; b < kBuckets; ++b) {
+        d.bl_off[b] = (int32_t)off;
+        int64_t cap = 0;
+        if (s.K > kRegK) {
+            if (b == 0) {
+                cap = s.N;
+            } else if (b < kWarpBucket) {
+                const int64_t lo = (int64_t)4 << b;  // 8, 16, 32, 64, 128
+                cap = lo < d.short_len ? std::min<int64_t>(s.N, d.E / (lo + 1)) : 0;
+            } else {
+                cap = std::min<int64_t>(s.N, d.E / ((int64_t)d.short_len + 1));
+            }
+        }
+        off += cap;
+    }
+    d.bl_off[kBuckets] = (int32_t)off;
     // one range per scatter CTA, as many ranges as CTAs fit at once on GB300's 152 SMs
     // (shared memory per CTA grows with the digit count; at most 4 CTAs by registers)
     const int maxbits = std::max(d.fbits, first_bits(d));
     const int per_sm = std::max<int>(1, std::min<int>(4, (int)(kSmemPerSM / (scatter_smem(maxbits) + 1024))));
     const int target = kSMs * per_sm;
-    d.range_tiles = std::max<int32_t>(1, (d.tiles_e + target - 1) / target);
-    d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
+    set_ranges(d, std::max<int32_t>(1, (d.tiles_e + target - 1) / target));
 }
 
 uint32_t hub_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / ((int64_t)d.hub_C + 1)); }
@@ -166,6 +211,7 @@ uint32_t chunk_cap_of(const GraphDesc &d) { return (uint32_t)(d.E / d.hub_C) + h
 // zero-initialised arrays of one graph (its status word is allocated by the caller)
 void layout_zero(Bump &b, GraphDesc &d) {
     d.rowcnt = b.take<int32_t>((size_t)d.N);
+    d.bcount = d.K > kRegK ? b.take<uint32_t>((size_t)kBuckets) : nullptr;
     d.nk = b.take<int32_t>((size_t)d.K);
     d.hist1 = b.take<uint32_t>((size_t)kHistCopies << first_bits(d));
     d.hist2 = d.npass == 2 ? b.take<uint32_t>((size_t)kHistCopies << d.fbits) : nullptr;
@@ -182,6 +228,7 @@ void layout_rest(Bump &b, GraphDesc &d, bool weighted) {
     d.deg = b.take<float>((size_t)d.N);
     d.dinv = b.take<float>((size_t)d.N);
     d.tab = b.take<int2>((size_t)d.N);
+    d.rowlist = d.K > kRegK ? b.take<int32_t>((size_t)d.bl_off[kBuckets]) : nullptr;
 }
 
 void layout_call_zero(Bump &b, CallBufs &cb) {
@@ -190,7 +237,8 @@ void layout_call_zero(Bump &b, CallBufs &cb) {
     cb.arrive_z = b.take<uint32_t>(cb.hub_cap);
 }
 
-void layout_call_rest(Bump &b, CallBufs &cb) {
+void layout_call_rest(Bump &b, CallBufs &cb, int32_t G) {
+    cb.bitem = b.take<uint32_t>((size_t)kBuckets * G + 1);
     cb.hubs = b.take<HubEntry>(cb.hub_cap);
     cb.chunk_off = b.take<uint32_t>((size_t)cb.hub_cap + 1);
     cb.chunk_hub = b.take<uint32_t>(cb.chunk_cap);
@@ -214,7 +262,10 @@ gee_opts opts_or_default(const gee_opts *o) {
 int check_opts(const gee_opts &o) {
     if (o.hub_threshold < 0 || o.lanes_per_row < 0 || o.lanes_per_row > 32 ||
         (o.lanes_per_row & (o.lanes_per_row - 1)) || o.rows_per_item < 0 || o.rows_per_item > 32 ||
-        (o.rows_per_item & (o.rows_per_item - 1)))
+        (o.rows_per_item & (o.rows_per_item - 1)) ||
+        !(o.vec_width == 0 || o.vec_width == 2 || o.vec_width == 4 || o.vec_width == 8) ||
+        !(o.short_len == 0 || o.short_len == 8 || o.short_len == 16 || o.short_len == 32 || o.short_len == 64 ||
+          o.short_len == 128 || o.short_len == 256))
         return GEE_ERR_ARG;
     return GEE_OK;
 }
@@ -235,6 +286,7 @@ struct LaunchPlan {
     int32_t items[kNumPfx];          // total items per kernel
     int b1max = 1, fmax = 1;         // widest digits (shared-memory size of k_scatter)
     bool any_two = false, any_wdeg = false, smem_acc = false;
+    int vec = 0;                     // ring slots per lane of k_spmm (0: automatic)
     void *zero_base = nullptr;
     size_t zero_bytes = 0;
 };
@@ -250,7 +302,7 @@ void plan_items(const GraphDesc &d, int32_t it[kNumPfx]) {
     it[kPfxOffs2] = (edges && two) ? ((1 << d.fbits) + 31) / 32 : 0;
     it[kPfxScatF] = d.ranges;
     it[kPfxScan] = d.tiles_n;
-    it[kPfxRows] = row_items;
+    it[kPfxRows] = d.K > kRegK ? 0 : row_items;  // K > 8: length-bucket items, counted on the device
     it[kPfxWRows] = d.wdeg ? row_items : 0;
 }
 
@@ -263,6 +315,8 @@ void plan_accumulate(LaunchPlan &lp, const GraphDesc &d) {
     lp.any_two = lp.any_two || d.npass == 2;
     lp.any_wdeg = lp.any_wdeg || d.wdeg;
     lp.smem_acc = lp.smem_acc || d.K > kRegK;
+    lp.vec = d.vec;  // every graph of a launch is planned with the same options
+    lp.base.cb.ringw = lp.base.cb.ringw || d.val != nullptr || d.w != nullptr;
 }
 
 // Phases of one call, in launch order (the GEE_NUM_PHASES list in gee.h).
@@ -319,6 +373,29 @@ using PhaseSink = std::function<int(const PhaseEvents &)>;
         }                                            \
     } while (0)
 
+// The product kernel (k_spmm) of a plan.  Every lane accumulates into a shared-memory
+// column of K (rounded up to 8) classes; graphs with K > 8 count their work items on the
+// device (length buckets), so they take a full grid.
+cudaError_t launch_product(const LaunchPlan &lp, const DeviceInfo &dev, const Ctx &c, cudaStream_t st) {
+    const CallBufs &cb = lp.base.cb;
+    const int64_t hub_grid_max = cb.hub_cap > 0 ? cb.chunk_cap : 0;
+    const int kpad = std::min(kMaxK, (std::max(1, cb.kmax) + 7) & ~7);
+    const int wi = cb.ringw ? 1 : 0;
+    // ring depth: the requested one (automatic: 8), made shallower while fewer than two
+    // CTAs of the kernel would fit on an SM
+    int ring = lp.vec > 0 ? lp.vec : 8;
+    auto occ_of = [&](int r) { return dev.occ_spmm[r >= 8 ? 2 : (r >= 4 ? 1 : 0)][kpad / 8 - 1][wi]; };
+    while (ring > 2 && occ_of(ring) < 2) ring >>= 1;
+    const int socc = std::max(1, occ_of(ring));
+    const int64_t row_items = lp.items[kPfxRows];
+    int64_t sneed = std::max<int64_t>(std::min<int64_t>(hub_grid_max, 2 * (int64_t)dev.sms),
+                                      (row_items + kWarps - 1) / kWarps);
+    if (lp.smem_acc) sneed = (int64_t)dev.sms * socc;
+    const int sgrid = (int)std::min<int64_t>(sneed, (int64_t)dev.sms * socc);
+    if (sgrid <= 0) return cudaSuccess;
+    return launch_spmm(c, sgrid, kpad, ring, st);
+}
+
 // Enqueue the path: the CSR build, degrees and node table, and (embed) the product with
 // its epilogue.  One kernel launch per phase covers every graph of the plan.
 int run_plan(const LaunchPlan &lp, const DeviceInfo &dev, cudaStream_t st, PhaseEvents *pe, bool embed) {
@@ -347,17 +424,34 @@ int run_plan(const LaunchPlan &lp, const DeviceInfo &dev, cudaStream_t st, Phase
                                             (wrow_items + kWarps - 1) / kWarps);
     const int wgrid = (int)std::min<int64_t>(wneed, (int64_t)dev.sms * dev.occ_wdeg);
     GEE_PHASE(kPhWdeg, lp.any_wdeg && wgrid > 0, launch_wdeg(ctx(kPfxWRows), wgrid, st));
-    const int sm = lp.smem_acc ? 1 : 0;
-    const int64_t row_items = lp.items[kPfxRows];
-    const int64_t sneed = std::max<int64_t>(std::min<int64_t>(hub_grid_max, 2 * (int64_t)dev.sms),
-                                            (row_items + kWarps - 1) / kWarps);
-    const int sgrid = (int)std::min<int64_t>(sneed, (int64_t)dev.sms * dev.occ_spmm[sm]);
-    GEE_PHASE(kPhSpmm, embed && sgrid > 0, launch_spmm(ctx(kPfxRows), sgrid, lp.smem_acc, st));
+    GEE_PHASE(kPhSpmm, embed, launch_product(lp, dev, ctx(kPfxRows), st));
     GEE_TRY(mark(pe, kNumPhases, st));
     return GEE_OK;
 }
 
 // ---- one graph ------------------------------------------------------------------------
+
+// FNV-1a hash of a single graph's plan (every scalar field) and of its workspace base: a
+// workspace holds what gee_reembed needs only if its last CSR build had the same stamp.
+uint32_t plan_stamp(const GraphDesc &d, const char *base) {
+    uint32_t h = 2166136261u;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint32_t)(v & 0xffu);
+            h *= 16777619u;
+            v >>= 8;
+        }
+    };
+    mix((uint64_t)d.E);
+    mix((uint64_t)(uint32_t)d.N | ((uint64_t)(uint32_t)d.K << 32));
+    mix(d.flags | ((uint64_t)(d.val != nullptr) << 32) | ((uint64_t)d.wdeg << 33));
+    const int32_t f[] = {d.nbits, d.ncols, d.pbits, d.row0, d.npass, d.lbits, d.fbits, d.hub_C, d.lpr_log2, d.tiles_e, d.tiles_n,
+                         d.scan_tile, d.rows_per_item, d.short_len, d.vec, d.range_tiles, d.ranges};
+    for (int32_t x : f) mix((uint64_t)(uint32_t)x);
+    for (int i = 0; i <= kBuckets; ++i) mix((uint64_t)(uint32_t)d.bl_off[i]);
+    mix((uint64_t)reinterpret_cast<uintptr_t>(base));
+    return h == 0u ? 1u : h;  // 0 is the value of a zeroed workspace
+}
 
 struct SinglePlan {
     GraphDesc d;
@@ -366,10 +460,17 @@ struct SinglePlan {
     size_t total_bytes = 0;
 };
 
-void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p) {
+// cols / row0: column range and first row of a row shard (cols < 0: a whole graph)
+void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p, int32_t cols = -1,
+                 int32_t row0 = 0) {
     std::memset(&p.d, 0, sizeof(p.d));
     std::memset(&p.cb, 0, sizeof(p.cb));
     plan_params(s, o, want_deg, p.d);
+    if (cols >= 0) {
+        p.d.ncols = cols;
+        p.d.pbits = std::max(1, bitlen(cols > 0 ? (uint32_t)(cols - 1) : 0u));
+        p.d.row0 = row0;
+    }
     p.cb.hub_cap = hub_cap_of(p.d);
     p.cb.chunk_cap = chunk_cap_of(p.d);
     p.cb.kmax = s.K;
@@ -379,8 +480,9 @@ void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, S
     layout_zero(b, p.d);
     p.zero_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
     layout_rest(b, p.d, s.weighted);
-    layout_call_rest(b, p.cb);
+    layout_call_rest(b, p.cb, 1);
     p.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
+    p.d.stamp = plan_stamp(p.d, base);
 }
 
 LaunchPlan launch_plan_single(const SinglePlan &p) {
@@ -461,11 +563,13 @@ struct EmbedKey {
     gee_opts o;
     size_t ws_bytes;
     bool timed;  // gee_embed_timed: the graph records the phase events
+    int kind;    // 0 gee_embed, 1 gee_reembed
     bool operator==(const EmbedKey &b) const {
-        return device == b.device && src == b.src && dst == b.dst && w == b.w && labels == b.labels && Z == b.Z &&
+        return device == b.device && kind == b.kind && src == b.src && dst == b.dst && w == b.w && labels == b.labels && Z == b.Z &&
                ws == b.ws && status == b.status && E == b.E && N == b.N && K == b.K && o.flags == b.o.flags &&
                o.hub_threshold == b.o.hub_threshold && o.lanes_per_row == b.o.lanes_per_row &&
-               o.rows_per_item == b.o.rows_per_item && ws_bytes == b.ws_bytes && timed == b.timed;
+               o.rows_per_item == b.o.rows_per_item && o.vec_width == b.o.vec_width &&
+               o.short_len == b.o.short_len && ws_bytes == b.ws_bytes && timed == b.timed;
     }
 };
 
@@ -627,6 +731,194 @@ int gee_embed(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int6
 
 }  // extern "C"
 
+// ---- re-embedding with new labels ----------------------------------------------------
+namespace gee {
+namespace {
+
+int reembed_impl(const int32_t *d_labels, int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts,
+                 float *d_Z, void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status) {
+    GEE_TRY(check_shape(E, N, K));
+    if (N > 0 && (!d_labels || !d_Z)) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    GEE_TRY(check_opts(o));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    SinglePlan p;
+    const Shape s{E, N, K, weighted != 0};
+    plan_single(s, o, false, nullptr, p);
+    GEE_TRY(check_ws(d_workspace, workspace_bytes, p.total_bytes));
+    plan_single(s, o, false, static_cast<char *>(d_workspace), p);
+    p.d.y = d_labels;
+    p.d.Z = d_Z;
+    const LaunchPlan lp = launch_plan_single(p);
+    auto enqueue = [&](cudaStream_t s2, PhaseEvents *) -> int {
+        // counters of the product kernel, hub-merge arrivals, status and n_k start at zero;
+        // the CSR, degrees, hub chunks and length buckets stay as the last build left them
+        GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs->ctr, 0, sizeof(p.cb.cs->ctr), s2)));
+        if (p.cb.hub_cap) GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.arrive_z, 0, sizeof(uint32_t) * p.cb.hub_cap, s2)));
+        GEE_TRY(cuda_check(cudaMemsetAsync(p.d.status, 0, sizeof(uint32_t), s2)));
+        GEE_TRY(cuda_check(cudaMemsetAsync(p.d.nk, 0, sizeof(int32_t) * (size_t)K, s2)));
+        Ctx c = lp.base;
+        c.prefix = lp.prefix[kPfxRows];
+        c.items = lp.items[kPfxRows];
+        GEE_TRY(cuda_check(launch_relabel(c, s2)));
+        GEE_TRY(cuda_check(launch_product(lp, dev, c, s2)));
+        if (d_status)
+            GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s2)));
+        return GEE_OK;
+    };
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GEE_TRY(cuda_check(cudaStreamIsCapturing(st, &cs)));
+    if ((o.flags & GEE_NO_GRAPH_CACHE) || cs != cudaStreamCaptureStatusNone) return enqueue(st, nullptr);
+    EmbedKey key;
+    std::memset(&key, 0, sizeof(key));
+    cudaGetDevice(&key.device);
+    key.kind = 1;
+    key.labels = d_labels;
+    key.Z = d_Z;
+    key.ws = d_workspace;
+    key.status = d_status;
+    key.w = weighted ? d_workspace : nullptr;
+    key.E = E;
+    key.N = N;
+    key.K = K;
+    key.o = o;
+    key.ws_bytes = workspace_bytes;
+    return launch_cached(key, st, enqueue, nullptr, nullptr);
+}
+
+}  // namespace
+}  // namespace gee
+
+extern "C" int gee_reembed(const int32_t *d_labels, int64_t E, int32_t N, int32_t K, int weighted,
+                           const gee_opts *opts, float *d_Z, void *d_workspace, size_t workspace_bytes, void *stream,
+                           uint32_t *d_status) {
+    return gee::reembed_impl(d_labels, E, N, K, weighted, opts, d_Z, d_workspace, workspace_bytes, stream,
+                             d_status);
+}
+
+// ---- row shards of one graph -------------------------------------------------------------
+namespace gee {
+namespace {
+
+int check_shard(int64_t E, int32_t N, int32_t r0, int32_t r1, int32_t K) {
+    GEE_TRY(check_shape(E, N, K));
+    if (r0 < 0 || r1 < r0 || r1 > N) return GEE_ERR_ARG;
+    return GEE_OK;
+}
+
+// The plan of rows [r0, r1) of a graph of N nodes (columns stay global ids).
+int shard_plan(int64_t E, int32_t N, int32_t r0, int32_t r1, int32_t K, int weighted, const gee_opts &o, void *ws,
+               size_t ws_bytes, SinglePlan &p) {
+    GEE_TRY(check_shard(E, N, r0, r1, K));
+    GEE_TRY(check_opts(o));
+    const Shape s{E, r1 - r0, K, weighted != 0};
+    plan_single(s, o, false, nullptr, p, N, r0);
+    if (ws == nullptr && ws_bytes == 0) return GEE_OK;  // sizing only
+    GEE_TRY(check_ws(ws, ws_bytes, p.total_bytes));
+    plan_single(s, o, false, static_cast<char *>(ws), p, N, r0);
+    return GEE_OK;
+}
+
+}  // namespace
+}  // namespace gee
+
+extern "C" {
+
+size_t gee_shard_workspace_size(int64_t E, int32_t N, int32_t r0, int32_t r1, int32_t K, int weighted,
+                                const gee_opts *opts) {
+    gee::SinglePlan p;
+    if (gee::shard_plan(E, N, r0, r1, K, weighted, gee::opts_or_default(opts), nullptr, 0, p) != GEE_OK) return 0;
+    return p.total_bytes;
+}
+
+int gee_shard_build(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N, int32_t r0,
+                    int32_t r1, const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_nk,
+                    void *d_workspace, size_t workspace_bytes, void *stream, uint32_t *d_status) {
+    using namespace gee;
+    GEE_TRY(check_inputs(d_src, d_dst, E, r1 - r0, d_labels));
+    if (!d_nk) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    SinglePlan p;
+    GEE_TRY(shard_plan(E, N, r0, r1, K, d_w != nullptr, o, d_workspace, workspace_bytes, p));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (r1 == r0) {
+        GEE_TRY(cuda_check(cudaMemsetAsync(d_nk, 0, sizeof(int32_t) * (size_t)K, st)));
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    p.d.src = d_src;
+    p.d.dst = d_dst;
+    p.d.w = d_w;
+    p.d.y = d_labels;
+    GEE_TRY(run_single(p, dev, st, nullptr, false));
+    GEE_TRY(cuda_check(cudaMemcpyAsync(d_nk, p.d.nk, sizeof(int32_t) * (size_t)K, cudaMemcpyDeviceToDevice, st)));
+    if (d_status)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+
+int gee_shard_table(int64_t E, int32_t N, int32_t r0, int32_t r1, const int32_t *d_labels, int32_t K, int weighted,
+                    const gee_opts *opts, const int32_t *d_nk, int32_t *d_tab, void *d_workspace,
+                    size_t workspace_bytes, void *stream) {
+    using namespace gee;
+    if (r1 > r0 && (!d_labels || !d_nk || !d_tab)) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    SinglePlan p;
+    GEE_TRY(shard_plan(E, N, r0, r1, K, weighted, o, d_workspace, workspace_bytes, p));
+    if (r1 == r0) return GEE_OK;
+    p.d.y = d_labels;
+    p.d.nk = const_cast<int32_t *>(d_nk);
+    p.d.tab = reinterpret_cast<int2 *>(d_tab);
+    Ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.g0 = p.d;
+    c.G = 1;
+    c.cb = p.cb;
+    return cuda_check(launch_nodetab(c, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int gee_shard_embed(int64_t E, int32_t N, int32_t r0, int32_t r1, const int32_t *d_labels, int32_t K, int weighted,
+                    const gee_opts *opts, const int32_t *d_tab, float *d_Z, void *d_workspace,
+                    size_t workspace_bytes, void *stream, uint32_t *d_status) {
+    using namespace gee;
+    if (r1 > r0 && (!d_labels || !d_tab || !d_Z)) return GEE_ERR_ARG;
+    const gee_opts o = opts_or_default(opts);
+    SinglePlan p;
+    GEE_TRY(shard_plan(E, N, r0, r1, K, weighted, o, d_workspace, workspace_bytes, p));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (r1 == r0) {
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    p.d.y = d_labels;
+    p.d.Z = d_Z;
+    p.d.tab = reinterpret_cast<int2 *>(const_cast<int32_t *>(d_tab));  // the gathered table of all N nodes
+    const LaunchPlan lp = launch_plan_single(p);
+    GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.cs->ctr, 0, sizeof(p.cb.cs->ctr), st)));
+    if (p.cb.hub_cap) GEE_TRY(cuda_check(cudaMemsetAsync(p.cb.arrive_z, 0, sizeof(uint32_t) * p.cb.hub_cap, st)));
+    GEE_TRY(cuda_check(cudaMemsetAsync(p.d.status, 0, sizeof(uint32_t), st)));
+    Ctx c = lp.base;
+    c.prefix = lp.prefix[kPfxRows];
+    c.items = lp.items[kPfxRows];
+    GEE_TRY(cuda_check(launch_stamp_check(c, st)));
+    GEE_TRY(cuda_check(launch_product(lp, dev, c, st)));
+    if (d_status)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, p.d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
+}
+
+}  // extern "C"
+
 // ---- autotuner --------------------------------------------------------------------------
 namespace gee {
 namespace {
@@ -646,42 +938,50 @@ std::vector<TuneEntry> *g_tune = nullptr;  // never freed
 
 bool same_opts(const gee_opts &a, const gee_opts &b) {
     return a.flags == b.flags && a.hub_threshold == b.hub_threshold && a.lanes_per_row == b.lanes_per_row &&
-           a.rows_per_item == b.rows_per_item;
+           a.rows_per_item == b.rows_per_item && a.vec_width == b.vec_width && a.short_len == b.short_len;
 }
 
-// Split thresholds and row-block sizes around the automatic ones (the caller's non-zero
-// fields stay fixed).
-std::vector<gee_opts> tune_candidates(const Shape &s, const gee_opts &o) {
+// The values the autotuner tries for each tuning field, around the automatic ones (a
+// field the caller set to a non-zero value stays fixed).  The search is by coordinates:
+// starting from the automatic options, each field in turn takes the value of its list
+// that runs fastest with the others at their best so far.
+struct TuneAxes {
+    std::vector<int32_t> vec, shortl, hub, rpi;
+};
+
+TuneAxes tune_axes(const Shape &s, const gee_opts &o) {
     GraphDesc d;
     std::memset(&d, 0, sizeof(d));
     plan_params(s, o, false, d);
-    std::vector<int32_t> hubs, rpis;
+    TuneAxes ax;
     auto add = [](std::vector<int32_t> &v, int32_t x) {
         if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
     };
-    if (o.hub_threshold > 0) {
-        add(hubs, o.hub_threshold);
-    } else {
-        add(hubs, d.hub_C);
-        add(hubs, std::max(1024, d.hub_C / 2));
-        add(hubs, d.hub_C * 2);
+    add(ax.vec, d.vec);
+    if (o.vec_width == 0)
+        for (int32_t v : {8, 4, 2}) add(ax.vec, v);
+    add(ax.shortl, d.short_len);
+    if (o.short_len == 0 && s.K > kRegK)
+        for (int32_t v : {16, 32, 64, 128, 256}) add(ax.shortl, v);
+    add(ax.hub, d.hub_C);
+    if (o.hub_threshold == 0) {
+        add(ax.hub, std::max(1024, d.hub_C / 2));
+        add(ax.hub, d.hub_C * 2);
     }
-    if (o.rows_per_item > 0) {
-        add(rpis, o.rows_per_item);
-    } else {
-        add(rpis, d.rows_per_item);
-        add(rpis, std::max(1, d.rows_per_item / 4));
-        add(rpis, std::min(32, d.rows_per_item * 4));
+    add(ax.rpi, d.rows_per_item);
+    if (o.rows_per_item == 0) {
+        add(ax.rpi, std::max(1, d.rows_per_item / 4));
+        add(ax.rpi, std::min(32, d.rows_per_item * 4));
     }
-    std::vector<gee_opts> out;
-    for (int32_t h : hubs)
-        for (int32_t r : rpis) {
-            gee_opts c = o;
-            c.hub_threshold = h;
-            c.rows_per_item = r;
-            out.push_back(c);
-        }
-    return out;
+    return ax;
+}
+
+gee_opts with_fields(gee_opts o, int32_t vec, int32_t shortl, int32_t hub, int32_t rpi) {
+    o.vec_width = vec;
+    o.short_len = shortl;
+    o.hub_threshold = hub;
+    o.rows_per_item = rpi;
+    return o;
 }
 
 }  // namespace
@@ -692,9 +992,13 @@ extern "C" {
 size_t gee_autotune_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts) {
     if (check_shape(E, N, K) != GEE_OK) return 0;
     const gee_opts o = opts_or_default(opts);
+    const TuneAxes ax = tune_axes(Shape{E, N, K, weighted != 0}, o);
     size_t m = 0;
-    for (const gee_opts &c : tune_candidates(Shape{E, N, K, weighted != 0}, o))
-        m = std::max(m, gee_workspace_size(E, N, K, weighted, &c));
+    for (int32_t h : ax.hub)
+        for (int32_t r : ax.rpi) {
+            const gee_opts c = with_fields(o, ax.vec[0], ax.shortl[0], h, r);
+            m = std::max(m, gee_workspace_size(E, N, K, weighted, &c));
+        }
     return m;
 }
 
@@ -727,29 +1031,47 @@ int gee_autotune(const int32_t *d_src, const int32_t *d_dst, const float *d_w, i
     }
     constexpr int kReps = 3;
     int rc = GEE_OK;
-    float best_t = -1.0f;
-    gee_opts pick = o;
-    for (const gee_opts &c : tune_candidates(Shape{E, N, K, d_w != nullptr}, o)) {
-        if (gee_workspace_size(E, N, K, d_w != nullptr, &c) > workspace_bytes) continue;
+    // mean time of kReps calls with candidate c (after one warm-up), or < 0 if it does not
+    // fit the workspace
+    auto time_of = [&](const gee_opts &c, float &ms) -> int {
+        ms = -1.0f;
+        if (gee_workspace_size(E, N, K, d_w != nullptr, &c) > workspace_bytes) return GEE_OK;
         gee_opts run = c;
         run.flags |= GEE_NO_GRAPH_CACHE;  // the candidates do not fill the launch cache
-        rc = gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes, stream,
-                       nullptr);  // warm-up
-        if (rc == GEE_OK) rc = cuda_check(cudaEventRecord(e0, st));
-        for (int i = 0; i < kReps && rc == GEE_OK; ++i)
-            rc = gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes, stream,
-                           nullptr);
-        if (rc == GEE_OK) rc = cuda_check(cudaEventRecord(e1, st));
-        if (rc == GEE_OK) rc = cuda_check(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        if (rc == GEE_OK) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1));
-        if (rc != GEE_OK) break;
+        GEE_TRY(gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes, stream,
+                          nullptr));  // warm-up
+        GEE_TRY(cuda_check(cudaEventRecord(e0, st)));
+        for (int i = 0; i < kReps; ++i)
+            GEE_TRY(gee_embed(d_src, d_dst, d_w, E, N, d_labels, K, &run, d_Z, d_workspace, workspace_bytes,
+                              stream, nullptr));
+        GEE_TRY(cuda_check(cudaEventRecord(e1, st)));
+        GEE_TRY(cuda_check(cudaEventSynchronize(e1)));
+        GEE_TRY(cuda_check(cudaEventElapsedTime(&ms, e0, e1)));
         ms /= kReps;
-        if (best_t < 0.0f || ms < best_t) {
-            best_t = ms;
-            pick = c;
+        return GEE_OK;
+    };
+    const TuneAxes ax = tune_axes(Shape{E, N, K, d_w != nullptr}, o);
+    int32_t cur[4] = {ax.vec[0], ax.shortl[0], ax.hub[0], ax.rpi[0]};
+    const std::vector<int32_t> *axes[4] = {&ax.vec, &ax.shortl, &ax.hub, &ax.rpi};
+    float best_t = -1.0f;
+    gee_opts pick = o;
+    rc = time_of(with_fields(o, cur[0], cur[1], cur[2], cur[3]), best_t);
+    if (rc == GEE_OK && best_t >= 0.0f) pick = with_fields(o, cur[0], cur[1], cur[2], cur[3]);
+    for (int a = 0; a < 4 && rc == GEE_OK; ++a)
+        for (int32_t v : *axes[a]) {
+            if (v == cur[a]) continue;
+            int32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
+            trial[a] = v;
+            const gee_opts c = with_fields(o, trial[0], trial[1], trial[2], trial[3]);
+            float ms = -1.0f;
+            rc = time_of(c, ms);
+            if (rc != GEE_OK) break;
+            if (ms >= 0.0f && (best_t < 0.0f || ms < best_t)) {
+                best_t = ms;
+                pick = c;
+                cur[a] = v;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != GEE_OK) return rc;
@@ -768,6 +1090,113 @@ int gee_autotune(const int32_t *d_src, const int32_t *d_dst, const float *d_w, i
     t.best = pick;
     t.ms = best_t;
     g_tune->push_back(t);
+    return GEE_OK;
+}
+
+// ---- persistent autotuner cache: one JSON object per line, keyed by the GPU's name ----
+namespace {
+
+std::string device_name(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string();
+    }
+    std::string n(prop.name);
+    for (char &ch : n)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+    return n;
+}
+
+}  // namespace
+
+int gee_tune_cache_save(const char *path) {
+    if (!path) return GEE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE *f = std::fopen(path, "w");
+    if (!f) return GEE_ERR_ARG;
+    std::fprintf(f, "{\"format\": \"gee-tune-1\", \"entries\": [\n");
+    size_t i = 0, n = g_tune ? g_tune->size() : 0;
+    if (g_tune)
+        for (const TuneEntry &t : *g_tune) {
+            const gee_opts &a = t.fixed, &b = t.best;
+            std::fprintf(f,
+                         "{\"gpu\": \"%s\", \"E\": %lld, \"N\": %d, \"K\": %d, \"weighted\": %d, "
+                         "\"fixed\": [%u, %d, %d, %d, %d, %d], \"best\": [%u, %d, %d, %d, %d, %d], \"ms\": %.9g}%s\n",
+                         device_name(t.device).c_str(), (long long)t.E, t.N, t.K, t.weighted, a.flags, a.hub_threshold,
+                         a.lanes_per_row, a.rows_per_item, a.vec_width, a.short_len, b.flags, b.hub_threshold,
+                         b.lanes_per_row, b.rows_per_item, b.vec_width, b.short_len, (double)t.ms,
+                         ++i < n ? "," : "");
+        }
+    std::fprintf(f, "]}\n");
+    return std::fclose(f) == 0 ? GEE_OK : GEE_ERR_ARG;
+}
+
+int gee_tune_cache_load(const char *path, int *loaded) {
+    if (loaded) *loaded = 0;
+    if (!path) return GEE_ERR_ARG;
+    int dev = 0;
+    const std::string here = cudaGetDevice(&dev) == cudaSuccess ? device_name(dev) : std::string();
+    FILE *f = std::fopen(path, "r");
+    if (!f) return GEE_ERR_ARG;
+    char line[1024];
+    int count = 0, rc = GEE_OK;
+    bool header = false;
+    std::vector<TuneEntry> add;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (std::strstr(line, "\"format\": \"gee-tune-1\"")) {
+            header = true;
+            continue;
+        }
+        if (!std::strstr(line, "\"gpu\"")) continue;
+        char gpu[256] = {0};
+        long long E = 0;
+        TuneEntry t;
+        std::memset(&t, 0, sizeof(t));
+        double ms = 0.0;
+        const int got = std::sscanf(
+            line,
+            " {\"gpu\": \"%255[^\"]\", \"E\": %lld, \"N\": %d, \"K\": %d, \"weighted\": %d, "
+            "\"fixed\": [%u, %d, %d, %d, %d, %d], \"best\": [%u, %d, %d, %d, %d, %d], \"ms\": %lf",
+            gpu, &E, &t.N, &t.K, &t.weighted, &t.fixed.flags, &t.fixed.hub_threshold, &t.fixed.lanes_per_row,
+            &t.fixed.rows_per_item, &t.fixed.vec_width, &t.fixed.short_len, &t.best.flags, &t.best.hub_threshold,
+            &t.best.lanes_per_row, &t.best.rows_per_item, &t.best.vec_width, &t.best.short_len, &ms);
+        if (got != 18) {
+            rc = GEE_ERR_ARG;  // a malformed entry: nothing of the file is taken
+            break;
+        }
+        if (here.empty() || here != gpu) continue;  // entries of other GPUs stay in the file only
+        if (check_shape(E, t.N, t.K) != GEE_OK || check_opts(t.best) != GEE_OK) {
+            rc = GEE_ERR_ARG;
+            break;
+        }
+        t.device = dev;
+        t.E = E;
+        t.ms = (float)ms;
+        add.push_back(t);
+    }
+    std::fclose(f);
+    if (rc == GEE_OK && !header) rc = GEE_ERR_ARG;
+    if (rc != GEE_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune) g_tune = new std::vector<TuneEntry>();
+    for (const TuneEntry &t : add) {
+        bool dup = false;
+        for (const TuneEntry &o : *g_tune)
+            dup = dup || (o.device == t.device && o.E == t.E && o.N == t.N && o.K == t.K &&
+                          o.weighted == t.weighted && same_opts(o.fixed, t.fixed));
+        if (!dup) {
+            g_tune->push_back(t);
+            ++count;
+        }
+    }
+    if (loaded) *loaded = count;
+    return GEE_OK;
+}
+
+int gee_tune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune) g_tune->clear();
     return GEE_OK;
 }
 
@@ -991,8 +1420,7 @@ int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base
         // ranges of at least 8 tiles (one CTA each, many graphs in flight); never more
         // ranges than the graph alone would use, so a batch needs no more workspace
         // than its graphs would separately.  Only how work is cut changes, never Z.
-        d.range_tiles = std::max(kBatchRangeTiles, d.range_tiles);
-        d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
+        set_ranges(d, std::max(kBatchRangeTiles, d.range_tiles));
         hub_cap += hub_cap_of(d);
         chunk_cap += chunk_cap_of(d);
         cb.kmax = std::max(cb.kmax, d.K);
@@ -1013,7 +1441,7 @@ int plan_batch(const gee_graph *graphs, int32_t G, const gee_opts &o, char *base
     L.meta_bytes = (reinterpret_cast<size_t>(L.d_prefix) + sizeof(int32_t) * (size_t)kNumPfx * (G + 1)) -
                    reinterpret_cast<size_t>(L.d_descs);
     for (int32_t g = 0; g < G; ++g) layout_rest(b, L.descs[g], graphs[g].w != nullptr);
-    layout_call_rest(b, cb);
+    layout_call_rest(b, cb, G);
     L.total_bytes = (b.off + kAlign - 1) & ~(kAlign - 1);
 
     LaunchPlan &lp = L.lp;

@@ -27,12 +27,21 @@ constexpr int kMaxK = 64;
 constexpr int kRegK = 8;                       // K <= 8: per-lane register accumulators
 constexpr int kHistCopies = 8;                 // digit totals are spread over 8 copies: fewer
                                                // atomics on one address at the end of k_prep
+// K > 8: light rows are listed by length in kBuckets buckets (k_rowscan): buckets 0-5 hold
+// rows of at most 8, 16, 32, 64, 128, 256 entries (up to short_len), taken one lane per
+// row; the last bucket holds the longer light rows, taken by a whole warp each.
+constexpr int kBuckets = 7;
+constexpr int kWarpBucket = kBuckets - 1;
 
 constexpr int kSpinLimit = 1 << 22;            // bounded copy waits: ~1 s, then GEE_STATUS_TIMEOUT
 
 // status bits (must equal GEE_STATUS_* in gee.h)
-constexpr uint32_t kStIndex = 1u, kStLabel = 2u, kStWeight = 4u, kStTimeout = 8u, kStInternal = 16u;
+constexpr uint32_t kStIndex = 1u, kStLabel = 2u, kStWeight = 4u, kStTimeout = 8u, kStInternal = 16u,
+                   kStStale = 32u;
 constexpr uint32_t kOptAug = 1u, kOptLap = 2u, kOptCor = 4u;
+constexpr uint32_t kSentinel = 0xffffffffu;  // first-pass value of a dropped element (the reverse
+                                             // copy of a self-loop); never a packed key: those
+                                             // use at most 31 bits
 
 struct GraphDesc {
     // inputs (device)
@@ -40,11 +49,17 @@ struct GraphDesc {
     const float *w;          // nullptr = unweighted
     const int32_t *y;
     float *Z;
-    int64_t E;
+    int64_t E;               // edges sorted into the CSR (2 x Ein with sym): capacity of the CSR
+    int64_t Ein;             // edges of the input arrays
+    int32_t sym;             // 1: every input edge (i, j, e), i != j, also gives (j, i, e)
     int32_t N, K;
     uint32_t flags;
     // plan
-    int32_t nbits;           // bits of a node id (>= 1)
+    int32_t nbits;           // bits of a row id (>= 1)
+    int32_t ncols;           // column ids are in [0, ncols): N for a whole graph, the global node
+                             // count for a row shard
+    int32_t pbits;           // bits of a column id (payload of the packed first-pass keys)
+    int32_t row0;            // global id of row 0 (0 for a whole graph, the first row of a shard)
     int32_t npass;           // radix passes: 1 (nbits <= kOnePassBits) or 2
     int32_t lbits;           // digit bits of the first pass (2-pass graphs)
     int32_t fbits;           // digit bits of the final pass
@@ -54,6 +69,10 @@ struct GraphDesc {
     int32_t tiles_n;         // ceil(N / scan_tile)
     int32_t scan_tile;       // rows per k_rowscan tile: 256..2048, whole final-digit groups
     int32_t rows_per_item;   // light rows per SpMM work item
+    int32_t short_len;       // K > 8: light rows of at most this many entries take one lane each
+    int32_t vec;             // 16-byte vectors per lane per round of the product loop (1, 2, 4)
+    int32_t bl_off[kBuckets + 1];  // K > 8: start of each bucket's list in rowlist, end last
+    uint32_t stamp;          // hash of the plan and workspace layout: what a re-embedding checks
     int32_t wdeg;            // 1: degrees and node table come from k_wdeg (weighted + Laplacian)
     int32_t range_tiles;     // sort tiles per range; one CTA scatters one range
     int32_t ranges;          // ceil(tiles_e / range_tiles)
@@ -72,6 +91,8 @@ struct GraphDesc {
     float *deg;              // [N]  D_ii
     float *dinv;             // [N]  D_ii^-1/2 (1 without the Laplacian)
     int2 *tab;               // [N]  {class or 0, s_j as float bits (0 if unlabelled)}
+    int32_t *rowlist;        // K > 8: [bl_off[kBuckets]] light rows by length bucket
+    uint32_t *bcount;        // K > 8: [kBuckets] zeroed: rows listed per bucket
     uint32_t *status;        // [1]           zeroed
 };
 
@@ -82,7 +103,9 @@ struct CallState {
     uint32_t ctr[8];         // work-stealing / tile-id counters, one per kernel
     uint32_t hub_count;      // rows longer than their graph's hub_C
     uint32_t hub_chunks;     // total chunks over those rows
-    uint32_t pad[6];
+    uint32_t light_items;    // k_spmm work items over the length buckets of all K > 8 graphs
+    uint32_t stamp;          // single graph: the plan stamp of the last completed CSR build
+    uint32_t pad[4];
 };
 
 struct HubEntry {
@@ -98,9 +121,11 @@ struct CallBufs {
     uint32_t *arrive_z;      // [hub_cap] zeroed
     double *part_deg;        // [chunk_cap]
     float2 *part_z;          // [chunk_cap * kmax]
+    uint32_t *bitem;         // [kBuckets * G + 1]: prefix of the bucket work items, longest bucket
+                             // first, graph by graph within a bucket
     uint32_t hub_cap, chunk_cap;
     int32_t kmax;            // largest K in the call
-    int32_t pad;
+    int32_t ringw;           // k_spmm: 1 if any graph of the call is weighted (a val ring too)
 };
 
 // Launch context: which graphs, and how this kernel's items map onto them.

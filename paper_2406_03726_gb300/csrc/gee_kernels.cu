@@ -138,6 +138,12 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
     return s;
 }
 
+// log2 of the lanes of a row of `len` entries: the smallest c with 8 * 2^c >= len, c <= 5
+__device__ __forceinline__ uint32_t lanes_log2_for(int len) {
+    if (len <= 8) return 0u;
+    return (uint32_t)min(5, 32 - __clz(len - 1) - 3);
+}
+
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
 // ------------------------------------------------------------------------------------
@@ -211,7 +217,29 @@ __device__ __forceinline__ int64_t range_begin(const GraphDesc &g, int r) {
     return (int64_t)r * g.range_tiles * kSortTile;
 }
 __device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
-    return (int)min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
+    const int64_t n = min64((int64_t)g.range_tiles * kSortTile, g.E - range_begin(g, r));
+    return n > 0 ? (int)n : 0;
+}
+
+// Range r of the (virtual) edge list as read from the input arrays: first edge e0 of the
+// input, length n, and whether the range reads the reverse copies.  Without symmetrizing
+// the ranges cut the input; with it, the first half of the ranges cuts the input read
+// forward and the second half the same input read with source and target swapped (the
+// reverse copies come after every forward edge: the CSR keeps each row's forward edges in
+// input order, then its reverse ones).
+__device__ __forceinline__ void coo_range(const GraphDesc &g, int r, int64_t &e0, int &n, bool &rev) {
+    const int64_t L = (int64_t)g.range_tiles * kSortTile;
+    if (!g.sym) {
+        rev = false;
+        e0 = range_begin(g, r);
+        n = range_len(g, r);
+        return;
+    }
+    const int rh = g.ranges >> 1;
+    rev = r >= rh;
+    e0 = (int64_t)(rev ? r - rh : r) * L;
+    const int64_t m = min64(L, g.Ein - e0);
+    n = m > 0 ? (int)m : 0;
 }
 
 // Stream the ids [0, n) of p through f(value), CTA-wide, through shared memory: stages of
@@ -299,10 +327,15 @@ __global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
         for (int i = tid; i < nh; i += kThreads) h[i] = 0;
         __syncthreads();
         uint32_t *hw = h + warp * str;
-        const uint32_t N = (uint32_t)sg.N;
+        const uint32_t N = (uint32_t)sg.N, R0 = (uint32_t)sg.row0;
         const uint32_t m = (1u << b1) - 1u;
         uint32_t parity = 0;
-        stream_ids_staged(sg.src + range_begin(sg, t), range_len(sg, t), ring, parity, err, [&](int v) {
+        int64_t e0;
+        int rn;
+        bool rev;
+        coo_range(sg, t, e0, rn, rev);
+        stream_ids_staged((rev ? sg.dst : sg.src) + e0, rn, ring, parity, err, [&](int v) {
+            v = (int)((uint32_t)v - R0);
             if ((uint32_t)v >= N) {
                 err |= kStIndex;
                 v = 0;
@@ -488,12 +521,13 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(int D) {
 }
 
 template <bool FINAL>
-__device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e0, int n, uint32_t *stage,
+__device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e0, int n, bool rev, uint32_t *stage,
                                                    uint64_t *bar) {
     const bool coo = !FINAL || g.npass == 1;
     const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
-    const void *p0 = coo ? (const void *)(g.src + e0) : (const void *)(g.tmpk + e0);
-    const void *p1 = coo ? (const void *)(g.dst + e0) : nullptr;
+    const int32_t *sp = rev ? g.dst : g.src, *dp = rev ? g.src : g.dst;  // reverse copies: swapped
+    const void *p0 = coo ? (const void *)(sp + e0) : (const void *)(g.tmpk + e0);
+    const void *p1 = coo ? (const void *)(dp + e0) : nullptr;
     const void *p2 = g.w ? (coo ? (const void *)(g.w + e0) : (const void *)(g.tmpw + e0)) : nullptr;
     const bool ok = bytes > 0 && aligned16(p0) && (!p1 || aligned16(p1)) && (!p2 || aligned16(p2));
     if (ok) {
@@ -509,17 +543,18 @@ __device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e
 
 constexpr uint32_t kNoKey = 0xffffffffu;
 
-// One element of a tile -> (digit, payload, weight).  Source ids >= N count as 0 (k_prep
-// flags them and counts them as 0 too); out-of-range targets are flagged and become 0.
-// Weights are checked by the pass that writes the CSR.
+// One element of a tile -> (digit, payload, weight).  Rows are source ids minus row0;
+// rows outside [0, N) count as 0 (k_prep flags them and counts them as 0 too); targets
+// outside [0, NC) are flagged and become 0.  Weights are checked by the pass that writes
+// the CSR.
 template <bool FINAL>
-__device__ __forceinline__ void scatter_item(bool coo, uint32_t a, uint32_t b, float x, uint32_t N, int lb, int nb,
-                                             uint32_t nmask, uint32_t dmask, bool has_w, bool lap, uint32_t &key,
-                                             uint32_t &pay, uint32_t &err) {
+__device__ __forceinline__ void scatter_item(bool coo, bool rev, uint32_t a, uint32_t b, float x, uint32_t N,
+                                             uint32_t R0, uint32_t NC, int lb, int nb, uint32_t nmask, uint32_t dmask,
+                                             bool has_w, bool lap, uint32_t &key, uint32_t &pay, uint32_t &err) {
     if (coo) {
-        const uint32_t s = a < N ? a : 0u;
+        const uint32_t s = a - R0 < N ? a - R0 : 0u;
         uint32_t d = b;
-        if (d >= N) {
+        if (d >= NC) {
             err |= kStIndex;
             d = 0;
         }
@@ -528,8 +563,13 @@ __device__ __forceinline__ void scatter_item(bool coo, uint32_t a, uint32_t b, f
             pay = d;
         } else {
             key = s & ((1u << lb) - 1u);
-            pay = ((s >> lb) << nb) | d;
+            // the reverse copy of a self-loop is dropped: it keeps its place in the first
+            // pass (k_prep counted it) but carries the sentinel, which the later passes skip
+            pay = (rev && a == b) ? kSentinel : (((s >> lb) << nb) | d);
         }
+    } else if (a == kSentinel) {
+        key = kNoKey;  // a dropped element: not ranked, not written
+        pay = 0;
     } else {
         key = (a >> nb) & dmask;  // < D for every packed value the first pass writes
         pay = a & nmask;
@@ -556,8 +596,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
     const int bbits = bits < 8 ? bits : 8;
     const uint32_t bmask = (uint32_t)BD - 1u;
     const bool sep = D <= kSepDigits;
-    const int nb = sg.nbits, lb = sg.lbits;
+    const int nb = sg.pbits, lb = sg.lbits;
     const uint32_t nmask = (1u << nb) - 1u;  // nb <= 21
+    const uint32_t R0 = (uint32_t)sg.row0, NC = (uint32_t)sg.ncols;
     const uint32_t dmask = (uint32_t)D - 1u;
     const bool has_w = sg.w != nullptr;
     const bool lap = (sg.flags & kOptLap) != 0;
@@ -580,15 +621,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
 
     const int dpt = (D + kThreads - 1) / kThreads;
     const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
-    const int64_t r0 = range_begin(sg, r);
-    const int rn = range_len(sg, r);
+    int64_t r0;
+    int rn;
+    bool rev = false;
+    if (coo) coo_range(sg, r, r0, rn, rev);
+    else {
+        r0 = range_begin(sg, r);
+        rn = range_len(sg, r);
+    }
     const int ntiles = (rn + kSortTile - 1) / kSortTile;
     uint32_t err = 0;
 
     if (tid == 0) {
         s_err = 0;
         mbar_init(&bar, 1);
-        s_staged = scatter_issue_stage<FINAL>(sg, r0, min(rn, kSortTile), stage, &bar);
+        s_staged = scatter_issue_stage<FINAL>(sg, r0, min(rn, kSortTile), rev, stage, &bar);
     }
     for (int i = tid; i < kWarps * BD; i += kThreads) bins[i] = 0u;
     for (int d = dlo; d < dhi; ++d) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
@@ -616,7 +663,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
                 const uint32_t a = stage[idx];
                 const uint32_t b = coo ? stage[kStreamWords + idx] : 0u;
                 wv[i] = has_w ? __uint_as_float(stage[2 * kStreamWords + idx]) : 1.0f;
-                scatter_item<FINAL>(coo, a, b, wv[i], N, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i], err);
+                scatter_item<FINAL>(coo, rev, a, b, wv[i], N, R0, NC, lb, nb, nmask, dmask, has_w, lap, key[i],
+                                    pay[i], err);
             }
         } else {
             const int nst = staged ? (n & ~3) : 0;
@@ -634,15 +682,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
                         if (coo) b = stage[kStreamWords + idx];
                         if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
                     } else if (coo) {
-                        a = (uint32_t)ld_stream(sg.src + e0 + idx);
-                        b = (uint32_t)ld_stream(sg.dst + e0 + idx);
+                        a = (uint32_t)ld_stream((rev ? sg.dst : sg.src) + e0 + idx);
+                        b = (uint32_t)ld_stream((rev ? sg.src : sg.dst) + e0 + idx);
                         if (has_w) x = ld_stream(sg.w + e0 + idx);
                     } else {
                         a = ld_stream(sg.tmpk + e0 + idx);
                         if (has_w) x = ld_stream(sg.tmpw + e0 + idx);
                     }
                     wv[i] = x;
-                    scatter_item<FINAL>(coo, a, b, x, N, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i], err);
+                    scatter_item<FINAL>(coo, rev, a, b, x, N, R0, NC, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i],
+                                        err);
                 }
             }
         }
@@ -651,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
         // ---- start streaming the next tile of this range
         if (tid == 0 && ti + 1 < ntiles)
             s_staged = scatter_issue_stage<FINAL>(sg, e0 + kSortTile, min(kSortTile, rn - (ti + 1) * kSortTile),
-                                                  stage, &bar);
+                                                  rev, stage, &bar);
 
         // ---- stable rank within the warp: peer masks, then a per-warp counter per digit
         for (int i = lane; i < D / 2; i += 32) reinterpret_cast<uint32_t *>(mycnt)[i] = 0u;
@@ -778,7 +827,7 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
     id_ring_init(ring);
     const int r = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     const int D2 = 1 << sg.fbits, D1 = 1 << sg.lbits;
-    const int nb = sg.nbits, lb = sg.lbits;
+    const int nb = sg.pbits, lb = sg.lbits;
     const int64_t e0 = range_begin(sg, r);
     const int n = range_len(sg, r);
     const uint32_t *lobase = sg.cnt1;  // row 0 of the first-pass offsets: the bucket bases
@@ -812,6 +861,7 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
             __syncthreads();
             stream_ids_staged(reinterpret_cast<const int32_t *>(sg.tmpk + ps), (int)(pe - ps), ring, parity, err,
                               [&](int v) {
+                if ((uint32_t)v == kSentinel) return;  // a dropped element
                 uint32_t hi = (uint32_t)v >> nb;
                 if (hi >= (uint32_t)D2) {
                     err |= kStInternal;
@@ -837,7 +887,9 @@ __global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
     } else {  // many tiny buckets: one atomic per edge
         for (int i = tid; i < n; i += kThreads) {
             const uint32_t p = (uint32_t)(e0 + i);
-            uint32_t hi = ld_stream(sg.tmpk + p) >> nb;
+            const uint32_t pv = ld_stream(sg.tmpk + p);
+            if (pv == kSentinel) continue;  // a dropped element
+            uint32_t hi = pv >> nb;
             if (hi >= (uint32_t)D2) {
                 err |= kStInternal;
                 hi = 0;
@@ -921,6 +973,37 @@ __device__ void hub_chunk_offsets(const CallBufs &cb, uint32_t *s_scan) {
     }
 }
 
+// Work items of the length buckets (k_spmm), by one CTA: bucket b of a K > 8 graph gives
+// ceil(count / 32) items (one row per item for the whole-warp bucket); the prefix runs
+// over (bucket, graph), longest bucket first, so long rows start early.
+__device__ void bucket_item_prefix(const Ctx &c, uint32_t *s_scan) {
+    const int G = c.G, nb = kBuckets * G;
+    uint32_t run = 0;
+    for (int b0 = 0; b0 < nb; b0 += kThreads) {
+        const int idx = b0 + threadIdx.x;
+        uint32_t v = 0;
+        if (idx < nb) {
+            const int bk = kWarpBucket - idx / G, g = idx % G;
+            const int K = G > 1 ? __ldg(&c.graphs[g].K) : c.g0.K;
+            if (K > kRegK) {
+                const uint32_t *bc = G > 1 ? c.graphs[g].bcount : c.g0.bcount;
+                const int lo = G > 1 ? __ldg(&c.graphs[g].bl_off[bk]) : c.g0.bl_off[bk];
+                const int hi = G > 1 ? __ldg(&c.graphs[g].bl_off[bk + 1]) : c.g0.bl_off[bk + 1];
+                const uint32_t cnt = min(__ldcg(bc + bk), (uint32_t)(hi - lo));
+                v = bk == kWarpBucket ? cnt : (cnt + 31u) / 32u;
+            }
+        }
+        uint32_t tot;
+        const uint32_t x = block_excl_scan(v, s_scan, tot);
+        if (idx < nb) c.cb.bitem[idx] = run + x;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        c.cb.bitem[nb] = run;
+        c.cb.cs->light_items = run;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
@@ -928,9 +1011,11 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     __shared__ int32_t buf[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_err;
     __shared__ int s_last;
+    __shared__ uint32_t s_bcnt[kBuckets], s_bbase[kBuckets];
 
     const int tid = threadIdx.x;
     if (tid == 0) s_err = 0;
+    if (tid < kBuckets) s_bcnt[tid] = 0;
     const int t = load_desc(c, blockIdx.x, &sg, sl, c.prefix);
     const int tile = sg.scan_tile, ipt = tile / kThreads;  // 1, 2, 4 or 8 rows per thread
     const int64_t n0 = (int64_t)t * tile;
@@ -971,30 +1056,53 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     }
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldcg(sg.nk + yv[k]) : 0;
+    const bool buckets = sg.K > kRegK;
+    int bks[kScanItems];       // K > 8: length bucket of each light row of this thread (-1: none)
+    uint32_t rk[kScanItems];   // its rank among this CTA's rows of that bucket
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int i = tid + k * kThreads;
-        if (i >= n) continue;
         const int64_t j = n0 + i;
-        const uint32_t ex = (uint32_t)buf[pad(i)];
-        const int32_t cnt = (int32_t)((i + 1 < tile ? (uint32_t)buf[pad(i + 1)] : tot) - ex);
-        const int32_t start = (int32_t)(base[k] + ex - (uint32_t)buf[pad(i & ~gmask)]);
-        sg.rowptr[j] = start;
-        if (i == n - 1 && n0 + n == sg.N) sg.rowptr[sg.N] = start + cnt;
-        if (cnt > sg.hub_C) {
-            const uint32_t h = atomicAdd(&c.cb.cs->hub_count, 1u);
-            if (h < c.cb.hub_cap) {
-                HubEntry he;
-                he.g = sl[1];
-                he.row = (int32_t)j;
-                he.len = cnt;
-                he.nch = (cnt + sg.hub_C - 1) / sg.hub_C;
-                c.cb.hubs[h] = he;
-            } else {
-                err |= kStInternal;  // capacity is sized so this cannot happen
+        bks[k] = -1;
+        rk[k] = 0;
+        if (i < n) {
+            const uint32_t ex = (uint32_t)buf[pad(i)];
+            const int32_t cnt = (int32_t)((i + 1 < tile ? (uint32_t)buf[pad(i + 1)] : tot) - ex);
+            const int32_t start = (int32_t)(base[k] + ex - (uint32_t)buf[pad(i & ~gmask)]);
+            sg.rowptr[j] = start;
+            if (i == n - 1 && n0 + n == sg.N) sg.rowptr[sg.N] = start + cnt;
+            if (cnt > sg.hub_C) {
+                const uint32_t h = atomicAdd(&c.cb.cs->hub_count, 1u);
+                if (h < c.cb.hub_cap) {
+                    HubEntry he;
+                    he.g = sl[1];
+                    he.row = (int32_t)j;
+                    he.len = cnt;
+                    he.nch = (cnt + sg.hub_C - 1) / sg.hub_C;
+                    c.cb.hubs[h] = he;
+                } else {
+                    err |= kStInternal;  // capacity is sized so this cannot happen
+                }
+            } else if (buckets) {
+                bks[k] = cnt > sg.short_len ? kWarpBucket : (int)lanes_log2_for(cnt);
+                rk[k] = atomicAdd(&s_bcnt[bks[k]], 1u);  // rank within the CTA (order is free)
             }
+            if (!sg.wdeg) write_node_known(sg, j, (float)cnt + aug, lap, yv[k], ny[k]);
         }
-        if (!sg.wdeg) write_node_known(sg, j, (float)cnt + aug, lap, yv[k], ny[k]);
+    }
+    // K > 8: one global atomic per bucket and CTA reserves the CTA's places in the lists
+    if (buckets) {
+        __syncthreads();
+        if (tid < kBuckets) s_bbase[tid] = s_bcnt[tid] ? atomicAdd(sg.bcount + tid, s_bcnt[tid]) : 0u;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int b = bks[k];
+            if (b < 0) continue;
+            const uint32_t pos = s_bbase[b] + rk[k];
+            if (pos < (uint32_t)(sg.bl_off[b + 1] - sg.bl_off[b])) sg.rowlist[sg.bl_off[b] + pos] = (int32_t)(n0 + tid + k * kThreads);
+            else err |= kStInternal;  // capacity is sized so this cannot happen
+        }
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();
@@ -1007,6 +1115,10 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
     if (s_last) {
         __threadfence();
         hub_chunk_offsets(c.cb, s_scan);
+        bucket_item_prefix(c, s_scan);
+        // a single graph's workspace now holds a complete CSR, degrees, hub chunks and
+        // length buckets for this plan: what gee_reembed may reuse
+        if (threadIdx.x == 0 && c.G == 1) c.cb.cs->stamp = c.g0.stamp;
     }
 }
 
@@ -1064,6 +1176,7 @@ __device__ __forceinline__ int warp_item_graph(const Ctx &c, uint32_t it, int &l
 
 // clamp a CSR row range to [0, E] (only matters after a reported failure)
 __device__ __forceinline__ void row_range(const GraphDesc &g, int64_t row, int64_t &s, int64_t &e) {
+    row = min(max(row, (int64_t)0), (int64_t)g.N - 1);
     s = __ldcg(g.rowptr + row);
     e = __ldcg(g.rowptr + row + 1);
     s = min(max(s, (int64_t)0), g.E);
@@ -1086,13 +1199,10 @@ __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
 // entries, 2 for <= 16, ..., 32 for rows longer than 128.  The lane count of a row
 // depends only on its length, so its floating-point sum order (and its bits) do not
 // depend on which rows share the block.  Rows longer than the split threshold belong
-// to the hub kernels and are skipped here.
+// to the hub kernels and are skipped here.  With K > 8, k_spmm takes rows of at most
+// short_len entries one lane per row instead (short_rows_smem), and the others with at
+// least 2 lanes.
 
-__device__ __forceinline__ uint32_t lanes_log2_for(int64_t len) {
-    uint32_t c = 0;
-    while (c < 5 && ((int64_t)8 << c) < len) ++c;
-    return c;
-}
 
 // ascending bitonic sort of one 32-bit key per lane
 __device__ __forceinline__ uint32_t warp_sort32(uint32_t key, int lane) {
@@ -1119,10 +1229,11 @@ struct BlockRow {
 };
 
 // Loads the block's rows (one round trip, two for k_wdeg's class sizes) and returns the
-// sorted (class << 5 | offset) keys; kNoRow for rows to skip (none, or hub rows).
+// sorted (class << 5 | offset) keys; kNoRow for rows to skip (none, hub rows, and rows of
+// at most short_len entries, which are flagged in is_short; short_len < 0: none).
 template <bool SPMM>
 __device__ __forceinline__ uint32_t load_block_rows(const GraphDesc &g, int64_t base, int nrows, int lane,
-                                                    BlockRow &br) {
+                                                    BlockRow &br, int short_len, bool &is_short) {
     const int64_t row = base + lane;
     const bool has = lane < nrows && row < g.N;
     br.rs = br.re = 0;
@@ -1133,7 +1244,7 @@ __device__ __forceinline__ uint32_t load_block_rows(const GraphDesc &g, int64_t 
     if (has) {
         const int32_t a = __ldcg(g.rowptr + row), b = __ldcg(g.rowptr + row + 1);
         if (SPMM) {
-            br.tab = __ldg(g.tab + row);
+            br.tab = __ldg(g.tab + g.row0 + row);
             if (g.flags & kOptLap) br.dinv = __ldg(g.dinv + row);
         } else {
             br.y = __ldg(g.y + row);
@@ -1144,7 +1255,11 @@ __device__ __forceinline__ uint32_t load_block_rows(const GraphDesc &g, int64_t 
     }
     if (!SPMM && br.y >= 0 && br.y < g.K) br.ny = __ldcg(g.nk + br.y);
     uint32_t key = kNoRow;
-    if (has && br.re - br.rs <= g.hub_C) key = (lanes_log2_for(br.re - br.rs) << 5) | (uint32_t)lane;
+    const int len = br.re - br.rs;
+    is_short = has && len <= short_len;
+    const uint32_t cmin = short_len >= 0 ? 1u : 0u;
+    if (has && !is_short && len <= g.hub_C) key = (max(cmin, lanes_log2_for(len)) << 5) | (uint32_t)lane;
+    if (nrows <= 1) return key;  // one row: already in order
     return warp_sort32(key, lane);
 }
 
@@ -1183,9 +1298,9 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
     __shared__ int s_last;
     __shared__ GraphDesc wd[kWarps];
     const int tid = threadIdx.x;
-    const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
+    const uint32_t hub_chunks = c.cb.hub_cap ? min(__ldcg(&c.cb.cs->hub_chunks), c.cb.chunk_cap) : 0u;
     for (int it = blockIdx.x; (uint32_t)it < hub_chunks; it = cta_next_item(&c.cb.cs->ctr[3], &s_it)) {
-        const int hub = (int)__ldcg(c.cb.chunk_hub + it);
+        const int hub = (int)min(__ldcg(c.cb.chunk_hub + it), c.cb.hub_cap - 1u);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
         load_desc_idx(c, he.g, &sg);
@@ -1217,7 +1332,7 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
             for (int k = 0; k < he.nch; ++k)
                 if (off + k < c.cb.chunk_cap) tot += __ldcg(c.cb.part_deg + off + k);
             const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
-            write_node(sg, he.row, (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
+            write_node(sg, min(max(he.row, 0), sg.N - 1), (float)(tot + (double)aug), (sg.flags & kOptLap) != 0);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1234,7 +1349,8 @@ __global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
         if (!sg.wdeg) continue;
         const int64_t base = (int64_t)blk * sg.rows_per_item;
         BlockRow br;
-        const uint32_t sk = load_block_rows<false>(sg, base, sg.rows_per_item, lane, br);
+        bool no_short;
+        const uint32_t sk = load_block_rows<false>(sg, base, sg.rows_per_item, lane, br, -1, no_short);
         for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr, int bi) {
             const int64_t rs = __shfl_sync(0xffffffffu, br.rs, bi), re = __shfl_sync(0xffffffffu, br.re, bi);
             const int yv = __shfl_sync(0xffffffffu, br.y, bi), ny = __shfl_sync(0xffffffffu, br.ny, bi);
@@ -1289,8 +1405,8 @@ template <int KR, int kVecs>
 __device__ __forceinline__ void acc_reg(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
                                         float (&acc)[KR], uint32_t &err) {
     const int64_t a0 = lo & ~(int64_t)3;
-    const bool has_w = g.val != nullptr && g.w != nullptr;
-    const uint32_t N = (uint32_t)g.N;
+    const bool has_w = g.val != nullptr;  // the CSR values exist exactly for weighted graphs
+    const uint32_t N = (uint32_t)g.ncols;
     const int64_t step = 4 * (int64_t)gsz;
     for (int64_t b = a0 + 4 * gl; b < hi; b += kVecs * step) {
         // kVecs 16-byte vectors of col (and val) in flight per lane, then their gathers
@@ -1329,8 +1445,8 @@ template <int kVecs>
 __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t hi, int gl, int gsz,
                                          float *sacc, int lane, uint32_t &tlo, uint32_t &thi, uint32_t &err) {
     const int64_t a0 = lo & ~(int64_t)3;
-    const bool has_w = g.val != nullptr && g.w != nullptr;
-    const uint32_t N = (uint32_t)g.N;
+    const bool has_w = g.val != nullptr;  // the CSR values exist exactly for weighted graphs
+    const uint32_t N = (uint32_t)g.ncols;
     const int64_t step = 4 * (int64_t)gsz;
     for (int64_t b = a0 + 4 * gl; b < hi; b += kVecs * step) {
         // kVecs 16-byte vectors of col (and val) in flight per lane, then their gathers
@@ -1361,6 +1477,122 @@ __device__ __forceinline__ void acc_smem(const GraphDesc &g, int64_t lo, int64_t
             }
         }
     }
+}
+
+// ---- light-row entry stream --------------------------------------------------------
+// stream_row adds e_ij s_j into slot y_j of the lane's shared-memory accumulator column
+// (col[32 k] is class k of this lane: every lane owns one bank, so the adds are free of
+// bank conflicts whatever the classes) for every entry of a row [rs, re), in order, taken
+// by lane gl of a group of lpr lanes: the lane's 16-byte vectors of col (and val) start at
+// (rs & ~3) + 4 gl and follow every 4 lpr entries.  They arrive through a private ring of
+// S slots in shared memory filled by cp.async (16-byte asynchronous copies, one commit
+// group per vector): S vectors of the lane are always in flight, without holding
+// registers, and each lane waits only for its own copies.  A slot is refilled once its
+// vector's gathers are issued (the gather addresses come from the slot, so the slot has
+// been read by then).  Only a vector that crosses the row's ends tests its entries; the
+// entries outside [rs, re) add +0 (exact no-ops).  Copies never read past the arrays
+// (col/val are padded by 4 entries) and gathers use clamped indices.  Every copy has
+// landed when the function returns.  32-bit indices: E < 2^30.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// This warp's ring: slot s of lane l at rc[32 s + l] (col) and rv[32 s + l] (val).
+struct Ring {
+    int4 *rc;
+    float4 *rv;
+};
+
+__device__ __forceinline__ int acc_slot(int k, int l) { return (k << 5) + l; }
+
+// Accumulators of stream_row: the lane's shared-memory column (any K), or for K <= 4
+// registers (no dependent shared-memory read-modify-write chain when consecutive entries
+// share a class).
+struct ColAcc {
+    float *col;
+    __device__ __forceinline__ void add(int c, float p) { col[(c & 63) << 5] += p; }
+};
+template <int KR>
+struct RegAcc {
+    float a[KR];
+    __device__ __forceinline__ void add(int c, float p) {
+#pragma unroll
+        for (int k = 0; k < KR; ++k) a[k] += (c == k) ? p : 0.0f;
+    }
+};
+
+template <int S, bool W, class A>
+__device__ __forceinline__ void stream_row(const GraphDesc &g, int rs, int re, int gl, int lpr, A &acc,
+                                           const Ring &ring, int lane) {
+    static_assert(S >= 2 && (S & (S - 1)) == 0, "ring depth");
+    const int step = 4 * lpr;
+    const uint32_t nmax = (uint32_t)g.ncols - 1u;
+    const int b0 = (rs & ~3) + 4 * gl;
+    const int nv = b0 < re ? (re - b0 + step - 1) / step : 0;  // vectors of this lane
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if (s < nv) {
+            cp_async16(ring.rc + 32 * s + lane, g.col + b0 + s * step);
+            if (W) cp_async16(ring.rv + 32 * s + lane, g.val + b0 + s * step);
+        }
+        cp_async_commit();
+    }
+    // two vectors per step: eight gathers in flight before the adds
+    for (int i = 0; i < nv; i += 2) {
+        cp_async_wait<S - 2>();  // the groups complete in order: vectors i and i + 1 have landed
+        int4 cv[2];
+        float4 wv[2];
+        int2 t[8];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int slot = 32 * ((i + u) & (S - 1)) + lane;
+            cv[u] = make_int4(0, 0, 0, 0);
+            wv[u] = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (i + u < nv) {
+                cv[u] = ring.rc[slot];
+                if (W) wv[u] = ring.rv[slot];
+            }
+            t[4 * u] = __ldg(g.tab + min((uint32_t)cv[u].x, nmax));
+            t[4 * u + 1] = __ldg(g.tab + min((uint32_t)cv[u].y, nmax));
+            t[4 * u + 2] = __ldg(g.tab + min((uint32_t)cv[u].z, nmax));
+            t[4 * u + 3] = __ldg(g.tab + min((uint32_t)cv[u].w, nmax));
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int slot = 32 * ((i + u) & (S - 1)) + lane;
+            if (i + u + S < nv) {
+                cp_async16(ring.rc + slot, g.col + b0 + (i + u + S) * step);
+                if (W) cp_async16(ring.rv + slot, g.val + b0 + (i + u + S) * step);
+            }
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (i + u >= nv) break;
+            const int bi = b0 + (i + u) * step;
+            const float ws[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
+            if (bi >= rs && bi + 4 <= re) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float sj = __int_as_float(t[4 * u + q].y);
+                    acc.add(t[4 * u + q].x, W ? ws[q] * sj : sj);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float sj = __int_as_float(t[4 * u + q].y);
+                    const bool in = bi + q >= rs && bi + q < re;
+                    acc.add(t[4 * u + q].x, in ? (W ? ws[q] * sj : sj) : 0.0f);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
 }
 
 // Epilogue of a row: augmentation term s_i on the row's own class, D_ii^-1/2 scaling
@@ -1396,121 +1628,160 @@ __device__ __forceinline__ float finish_entry(float total, int k, const RowTail 
     return v;
 }
 
-// one light row per lane group, K <= 8: register accumulators, butterfly over the group
+// Epilogue of one light row per lane group, K <= 8, from the lane's partial sums a[KR]:
+// a butterfly over the group adds them up, and the group stores the finished row.
 template <int KR>
-__device__ __forceinline__ void light_row_reg(const GraphDesc &g, int64_t row, int64_t rs, int64_t re,
-                                              const RowTail &rt, int gl, int lpr, uint32_t &err) {
-    float acc[KR];
-#pragma unroll
-    for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
-    const bool active = row < g.N;
-    if (active) {
-        if (lpr == 32) acc_reg<KR, 4>(g, rs, re, gl, lpr, acc, err);
-        else acc_reg<KR, 2>(g, rs, re, gl, lpr, acc, err);
-    }
+__device__ __forceinline__ void light_row_reg(const GraphDesc &g, int row, const RowTail &rt, int gl, int lpr,
+                                              float (&a)[KR]) {
 #pragma unroll
     for (int k = 0; k < KR; ++k)
-        for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (!active) return;
+        for (int o = lpr >> 1; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+    if (row >= g.N) return;
     const int K = g.K;
     float ss = 0.0f;
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
-        acc[k] = (k < K) ? finish_entry(acc[k], k, rt) : 0.0f;
-        ss += acc[k] * acc[k];
+        a[k] = (k < K) ? finish_entry(a[k], k, rt) : 0.0f;
+        ss += a[k] * a[k];
     }
     const float sc = row_scale(ss, rt.cor);
-    float *z = g.Z + row * (int64_t)K;
+    float *z = g.Z + (int64_t)row * K;
     for (int k = gl; k < K; k += lpr) {
         float v = 0.0f;
 #pragma unroll
-        for (int kk = 0; kk < KR; ++kk) v = (kk == k) ? acc[kk] : v;
+        for (int kk = 0; kk < KR; ++kk) v = (kk == k) ? a[kk] : v;
         z[k] = v * sc;
     }
 }
 
-// one light row per lane group, 8 < K <= 64: per-lane shared-memory columns.  The
-// accumulator is all-zero between rows; only the classes the row touched are reduced
-// (lane gl of the group owns the classes k = gl mod lpr and visits just the touched ones,
-// reading the group's columns in a rotated order, free of bank conflicts) and cleared.
-__device__ __forceinline__ uint64_t owned_classes(int gl, int lpr) {
-    // bits k with k mod lpr == gl
-    uint64_t m = 0;
-    switch (lpr) {
-        case 1: m = ~0ull; break;
-        case 2: m = 0x5555555555555555ull; break;
-        case 4: m = 0x1111111111111111ull; break;
-        case 8: m = 0x0101010101010101ull; break;
-        case 16: m = 0x0001000100010001ull; break;
-        default: m = 0x0000000100000001ull; break;
+// one light row per lane group, K <= 8: K <= 4 accumulates in registers, 5 <= K <= 8 in
+// the lane's shared-memory column (then taken into registers, clearing the slots)
+template <int KR, int V, bool W>
+__device__ __forceinline__ void light_row_small(const GraphDesc &g, int row, int rs, int re, const RowTail &rt,
+                                                int gl, int lpr, float *sacc, const Ring &ring, int lane) {
+    float a[KR];
+    if (KR <= 4) {
+        RegAcc<KR> acc;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) acc.a[k] = 0.0f;
+        if (row < g.N) stream_row<V, W>(g, rs, re, gl, lpr, acc, ring, lane);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) a[k] = acc.a[k];
+    } else {
+        ColAcc acc{sacc + lane};
+        if (row < g.N) stream_row<V, W>(g, rs, re, gl, lpr, acc, ring, lane);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            a[k] = acc.col[k << 5];
+            acc.col[k << 5] = 0.0f;
+        }
     }
-    return m << gl;
+    light_row_reg<KR>(g, row, rt, gl, lpr, a);
 }
 
-__device__ __forceinline__ void light_row_smem(const GraphDesc &g, int64_t row, int64_t rs, int64_t re,
-                                               const RowTail &rt, int gl, int lpr, float *sacc, int lane,
-                                               uint32_t &err) {
+// one light row per group of lpr >= 2 lanes, 8 < K <= 64: every lane accumulates its
+// share of the entries in its own shared-memory column; lane gl then owns the classes
+// k = gl mod lpr and sums the group's lpr slots of each, starting at its own lane and
+// going round (a fixed order per class, and at every step the lanes of the warp read
+// distinct banks), zeroing them; it finishes the entry and keeps it in its own slot until
+// the row's scale is known, then stores it.
+template <int V, bool W>
+__device__ __forceinline__ void long_row_smem(const GraphDesc &g, int row, int rs, int re, const RowTail &rt,
+                                              int gl, int lpr, float *sacc, const Ring &ring, int lane) {
     const int K = g.K;
     const int g0 = lane - gl;
-    uint32_t tlo = 0, thi = 0;
     const bool active = row < g.N;
-    if (active) {
-        if (lpr == 32) acc_smem<4>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
-        else acc_smem<2>(g, rs, re, gl, lpr, sacc, lane, tlo, thi, err);
-        if (rt.aug) {  // the augmentation term lands on the row's own class
-            if (rt.yi < 32) tlo |= 1u << rt.yi;
-            else thi |= 1u << (rt.yi - 32);
-        }
-    }
-    for (int o = lpr >> 1; o > 0; o >>= 1) {
-        tlo |= __shfl_xor_sync(0xffffffffu, tlo, o);
-        thi |= __shfl_xor_sync(0xffffffffu, thi, o);
-    }
+    ColAcc acc{sacc + lane};
+    if (active) stream_row<V, W>(g, rs, re, gl, lpr, acc, ring, lane);
     __syncwarp();
-    const uint64_t mine = (((uint64_t)thi << 32) | tlo) & owned_classes(gl, lpr);
     float ss = 0.0f;
-    for (uint64_t m = mine; m; m &= m - 1) {
-        const int k = __ffsll((long long)m) - 1;
-        float tot = 0.0f;
-        for (int j = 0; j < lpr; ++j) {
-            float *p = sacc + k * 32 + g0 + ((j + gl) & (lpr - 1));
-            tot += *p;
+    if (active)
+        for (int k = gl; k < K; k += lpr) {
+            float tot = 0.0f;
+            for (int j = 0; j < lpr; ++j) {
+                float *p = sacc + acc_slot(k, g0 + ((j + gl) & (lpr - 1)));
+                tot += *p;
+                *p = 0.0f;
+            }
+            const float v = finish_entry(tot, k, rt);
+            ss += v * v;
+            sacc[acc_slot(k, lane)] = v;
+        }
+    for (int o = lpr >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (active) {
+        const float sc = row_scale(ss, rt.cor);
+        float *z = g.Z + (int64_t)row * K;
+        for (int k = gl; k < K; k += lpr) {
+            float *p = sacc + acc_slot(k, lane);
+            z[k] = *p * sc;
             *p = 0.0f;
         }
-        const float v = finish_entry(tot, k, rt);
-        ss += v * v;
-        sacc[k * 32 + lane] = v;  // kept in this lane's own column until it is stored
     }
-    for (int o = lpr >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (!active) return;
-    const float sc = row_scale(ss, rt.cor);
-    float *z = g.Z + row * (int64_t)K;
-    auto take = [&](uint64_t m, int k) -> float {  // finished entry k of this lane, cleared
-        float v = 0.0f;
-        if (m & 1ull) {
-            v = sacc[k * 32 + lane] * sc;
-            sacc[k * 32 + lane] = 0.0f;
+    // every lane, active or not: the reduction above zeroed slots of other lanes' columns,
+    // which the next pass accumulates into
+    __syncwarp();
+}
+
+// Up to 32 rows of one length bucket, 8 < K <= 64: one lane per row (rows of similar
+// length, so the lanes stay busy together), accumulating into its own column with no
+// reduction.  The lane then adds the augmentation term and takes the row's scale
+// D_ii^-1/2 / ||Z_i|| from its column.  Z is written 8 classes at a time: each lane moves
+// its 8 values of the chunk into a transposed 32 x 8 tile laid over the chunk's own slots
+// (entry (r, c) at 8 r + (c ^ (r / 4 mod 8)): conflict-free both when the 32 lanes write
+// one class each and when they read 4 rows x 8 classes), then each store instruction
+// writes 32 contiguous bytes of each of 4 rows.  `rows` holds the rows (cnt of them).
+template <int V, bool W>
+__device__ __forceinline__ void bucket_rows(const GraphDesc &g, const int32_t *rows, int cnt, float *sacc,
+                                            const Ring &ring, int lane) {
+    const int K = g.K;
+    const bool has = lane < cnt;
+    int row = 0;
+    float mult = 0.0f;
+    if (has) {
+        row = min(max(__ldcg(rows + lane), 0), g.N - 1);
+        int64_t rs, re;
+        row_range(g, row, rs, re);
+        ColAcc acc{sacc + lane};
+        stream_row<V, W>(g, (int)rs, (int)re, 0, 1, acc, ring, lane);
+        const RowTail rt = row_tail(g, __ldg(g.tab + g.row0 + row), (g.flags & kOptLap) ? __ldg(g.dinv + row) : 1.0f);
+        if (rt.aug && rt.si != 0.0f) sacc[acc_slot(rt.yi & 63, lane)] += rt.si;
+        float ss = 0.0f;
+        if (rt.cor)
+            for (int k = 0; k < K; ++k) {
+                const float v = sacc[acc_slot(k, lane)] * rt.dv;
+                ss += v * v;
+            }
+        mult = rt.dv * row_scale(ss, rt.cor);
+    }
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        float *tile = sacc + (k0 << 5);  // the 256 slots of classes k0 .. k0+7
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = tile[(c << 5) + lane];
+        __syncwarp();
+        const int sw = (lane >> 2) & 7;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) tile[(lane << 3) + (c ^ sw)] = v[c];
+        __syncwarp();
+        const int c = lane & 7;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = 4 * q + (lane >> 3);
+            const float m = __shfl_sync(0xffffffffu, mult, r);
+            const int rr = __shfl_sync(0xffffffffu, row, r);
+            if (r < cnt && k0 + c < K) g.Z[(int64_t)rr * K + k0 + c] = tile[(r << 3) + (c ^ (q & 7))] * m;
         }
-        return v;
-    };
-    if (lpr == 1 && (K & 3) == 0) {  // the lane writes its whole row: 16-byte stores
-        float4 *z4 = reinterpret_cast<float4 *>(z);
-        uint64_t m = mine;
-        for (int k = 0; k < K; k += 4, m >>= 4)
-            z4[k >> 2] = make_float4(take(m, k), take(m >> 1, k + 1), take(m >> 2, k + 2), take(m >> 3, k + 3));
-    } else if (lpr == 1 && (K & 1) == 0) {  // 8-byte stores
-        float2 *z2 = reinterpret_cast<float2 *>(z);
-        uint64_t m = mine;
-        for (int k = 0; k < K; k += 2, m >>= 2) z2[k >> 1] = make_float2(take(m, k), take(m >> 1, k + 1));
-    } else {
-        uint64_t m = mine >> gl;
-        for (int k = gl; k < K; k += lpr, m >>= lpr) z[k] = take(m, k);
+        __syncwarp();
+        float4 *t4 = reinterpret_cast<float4 *>(tile);
+        t4[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        t4[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
     }
 }
 
 // One chunk of a hub row, processed by the whole CTA; the last CTA of the row merges.
 template <int KR>
-__device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, int hub, int chunk, float *sacc,
+__device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, int hub, int chunk, float *wa,
                           float *wtot, int *s_last, uint32_t &err) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = g.K;
@@ -1534,7 +1805,6 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
             for (int k = 0; k < KR; ++k)
                 if (k < K) wtot[warp * kMaxK + k] = acc[k];
     } else {
-        float *wa = sacc + warp * kMaxK * 32;
         for (int k = 0; k < K; ++k) wa[k * 32 + lane] = 0.0f;
         __syncwarp();
         uint32_t tlo = 0, thi = 0;
@@ -1569,7 +1839,8 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
     if (!*s_last) return;
     __threadfence();
     // last chunk to finish: merge all chunks of the row in chunk order
-    const RowTail rt = row_tail(g, __ldg(g.tab + he.row), (g.flags & kOptLap) ? __ldg(g.dinv + he.row) : 1.0f);
+    const int hrow = min(max(he.row, 0), g.N - 1);
+    const RowTail rt = row_tail(g, __ldg(g.tab + g.row0 + hrow), (g.flags & kOptLap) ? __ldg(g.dinv + hrow) : 1.0f);
     if (tid < K) {
         float S = 0.0f, C = 0.0f;
         for (int ch = 0; ch < he.nch; ++ch) {
@@ -1589,48 +1860,141 @@ __device__ void hub_chunk(const Ctx &c, const GraphDesc &g, const HubEntry &he, 
         wtot[kMaxK * kWarps - 1] = ss;
     }
     __syncthreads();
-    if (tid < K) g.Z[(int64_t)he.row * K + tid] = wtot[tid] * row_scale(wtot[kMaxK * kWarps - 1], rt.cor);
+    if (tid < K) g.Z[(int64_t)hrow * K + tid] = wtot[tid] * row_scale(wtot[kMaxK * kWarps - 1], rt.cor);
 }
 
-constexpr int kSmemAccBytes = kWarps * kMaxK * 32 * 4;  // 64 KB
+// One block of rows_per_item consecutive light rows of a K <= 8 graph (k_spmm): the rows
+// are loaded once (lane = row), then run in length-class passes.
+template <int V, bool W>
+__device__ __forceinline__ void spmm_block(const GraphDesc &sg, int64_t base, float *sacc, const Ring &ring,
+                                           int lane) {
+    const int K = sg.K;
+    BlockRow br;
+    bool no_short;
+    const uint32_t sk = load_block_rows<true>(sg, base, sg.rows_per_item, lane, br, -1, no_short);
+    for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr, int bi) {
+        const int rs = __shfl_sync(0xffffffffu, br.rs, bi), re = __shfl_sync(0xffffffffu, br.re, bi);
+        int2 t;
+        t.x = __shfl_sync(0xffffffffu, br.tab.x, bi);
+        t.y = __shfl_sync(0xffffffffu, br.tab.y, bi);
+        const RowTail rt = row_tail(sg, t, __shfl_sync(0xffffffffu, br.dinv, bi));
+        const int r = (int)row;
+        if (K <= 1) light_row_small<1, V, W>(sg, r, rs, re, rt, gl, lpr, sacc, ring, lane);
+        else if (K <= 2) light_row_small<2, V, W>(sg, r, rs, re, rt, gl, lpr, sacc, ring, lane);
+        else if (K <= 4) light_row_small<4, V, W>(sg, r, rs, re, rt, gl, lpr, sacc, ring, lane);
+        else light_row_small<8, V, W>(sg, r, rs, re, rt, gl, lpr, sacc, ring, lane);
+    });
+}
+
+// One work item of the length buckets of a K > 8 graph: up to 32 rows of a lane-per-row
+// bucket, or one row of the whole-warp bucket.
+template <int V, bool W>
+__device__ __forceinline__ void spmm_bucket_item(const GraphDesc &sg, int bk, uint32_t local, float *sacc,
+                                                 const Ring &ring, int lane) {
+    const int32_t *list = sg.rowlist + sg.bl_off[bk];
+    const uint32_t cap = (uint32_t)(sg.bl_off[bk + 1] - sg.bl_off[bk]);
+    const uint32_t count = min(__ldcg(sg.bcount + bk), cap);
+    if (bk == kWarpBucket) {
+        if (local >= count) return;
+        const int row = min(max(__ldcg(list + local), 0), sg.N - 1);
+        int64_t rs, re;
+        row_range(sg, row, rs, re);
+        const RowTail rt = row_tail(sg, __ldg(sg.tab + sg.row0 + row), (sg.flags & kOptLap) ? __ldg(sg.dinv + row) : 1.0f);
+        long_row_smem<V, W>(sg, row, (int)rs, (int)re, rt, lane, 32, sacc, ring, lane);
+    } else {
+        const uint32_t first = local * 32u;
+        if (first >= count) return;
+        bucket_rows<V, W>(sg, list + first, (int)min(32u, count - first), sacc, ring, lane);
+    }
+}
+
 
 // k_spmm: Z with the fused epilogue.
 //   hub rows   the CTA takes one chunk at a time (two-sum partials; the last CTA of a
 //              row merges them in chunk order and runs the epilogue)
 //   light rows then persistent warps, each claiming blocks of rows_per_item rows
-__global__ void __launch_bounds__(kThreads, 3) k_spmm(Ctx c) {
-    extern __shared__ __align__(16) float sacc_all[];
+// Resident CTAs per SM the product kernel is compiled for: the 4-vector stream needs
+// more registers per thread, so it runs 16 warps per SM instead of 24.
+template <int V>
+struct SpmmOcc {
+    static constexpr int kMinBlocks = 3;
+};
+
+template <int V>
+__global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(Ctx c) {
+    extern __shared__ __align__(16) unsigned char spmm_smem_all[];
     __shared__ GraphDesc sg;
     __shared__ int s_it;
     __shared__ int s_last;
     __shared__ float wtot[kWarps * kMaxK];
     __shared__ GraphDesc wd[kWarps];
-    const uint32_t hub_chunks = __ldcg(&c.cb.cs->hub_chunks);
+    const uint32_t hub_chunks = c.cb.hub_cap ? min(__ldcg(&c.cb.cs->hub_chunks), c.cb.chunk_cap) : 0u;
+    const int kpad = (c.cb.kmax + 7) & ~7;  // accumulator classes per lane: K rounded up to 8
+    // per warp: the accumulator [kpad][32] floats, then the col ring [V][32] int4, then (if
+    // any graph is weighted) the val ring [V][32] float4
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t wstride = (size_t)kpad * 128 + (size_t)V * 512 * (c.cb.ringw ? 2 : 1);
+    unsigned char *wbase = spmm_smem_all + warp * wstride;
+    float *sacc = reinterpret_cast<float *>(wbase);
+    const Ring ring{reinterpret_cast<int4 *>(wbase + (size_t)kpad * 128),
+                    reinterpret_cast<float4 *>(wbase + (size_t)kpad * 128 + (size_t)V * 512)};
     uint32_t err = 0;
     for (int it = blockIdx.x; (uint32_t)it < hub_chunks; it = cta_next_item(&c.cb.cs->ctr[4], &s_it)) {
-        const int hub = (int)__ldcg(c.cb.chunk_hub + it);
+        const int hub = (int)min(__ldcg(c.cb.chunk_hub + it), c.cb.hub_cap - 1u);
         const int chunk = it - (int)__ldcg(c.cb.chunk_off + hub);
         const HubEntry he = c.cb.hubs[hub];
         load_desc_idx(c, he.g, &sg);
         const int K = sg.K;
-        if (K <= 1) hub_chunk<1>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
-        else if (K <= 2) hub_chunk<2>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
-        else if (K <= 4) hub_chunk<4>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
-        else if (K <= 8) hub_chunk<8>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
-        else hub_chunk<0>(c, sg, he, hub, chunk, sacc_all, wtot, &s_last, err);
+        if (K <= 1) hub_chunk<1>(c, sg, he, hub, chunk, sacc, wtot, &s_last, err);
+        else if (K <= 2) hub_chunk<2>(c, sg, he, hub, chunk, sacc, wtot, &s_last, err);
+        else if (K <= 4) hub_chunk<4>(c, sg, he, hub, chunk, sacc, wtot, &s_last, err);
+        else if (K <= 8) hub_chunk<8>(c, sg, he, hub, chunk, sacc, wtot, &s_last, err);
+        else hub_chunk<0>(c, sg, he, hub, chunk, sacc, wtot, &s_last, err);
         if (err) {
             atomicOr(sg.status, err);
             err = 0;
         }
     }
     __syncthreads();  // the chunks are done with the accumulator space
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *sacc = sacc_all + warp * kMaxK * 32;
-    if (c.cb.kmax > kRegK)
-        for (int i = lane; i < kMaxK * 32; i += 32) sacc[i] = 0.0f;
+    for (int i = lane; i < kpad * 32; i += 32) sacc[i] = 0.0f;
     __syncwarp();
+    // length-bucket items of the K > 8 graphs (prefix built by k_rowscan's last CTA)
+    const uint32_t nbucket = __ldcg(&c.cb.cs->light_items);
+    const int nb = kBuckets * c.G;
     int cur = -1;
-    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items; it = warp_next_item(&c.cb.cs->ctr[5])) {
+    // the claim of a warp's next item is issued when it starts an item, so the atomic's
+    // round trip overlaps the work
+    uint32_t next_raw = 0;
+    for (uint32_t it = warp_first_item(); it < nbucket;
+         it = __shfl_sync(0xffffffffu, next_raw, 0) + gridDim.x * kWarps) {
+        if (lane == 0) next_raw = atomicAdd(&c.cb.cs->ctr[7], 1u);
+        int idx = 0;
+        if (lane == 0) {  // largest idx with bitem[idx] <= it
+            int lo = 0, hi = nb;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldcg(c.cb.bitem + mid) <= it) lo = mid;
+                else hi = mid;
+            }
+            idx = lo;
+        }
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        const int bk = kWarpBucket - idx / c.G, g = idx % c.G;
+        const uint32_t local = it - __ldcg(c.cb.bitem + idx);
+        if (g != cur) {
+            __syncwarp();
+            warp_load_desc(c, g, &wd[warp]);
+            cur = g;
+        }
+        const GraphDesc &sg = wd[warp];
+        if (sg.val) spmm_bucket_item<V, true>(sg, bk, local, sacc, ring, lane);
+        else spmm_bucket_item<V, false>(sg, bk, local, sacc, ring, lane);
+    }
+    // blocks of consecutive light rows of the K <= 8 graphs
+    cur = -1;
+    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items;
+         it = __shfl_sync(0xffffffffu, next_raw, 0) + gridDim.x * kWarps) {
+        if (lane == 0) next_raw = atomicAdd(&c.cb.cs->ctr[5], 1u);
         int blk;
         const int g = warp_item_graph(c, it, blk);
         if (g != cur) {
@@ -1639,27 +2003,95 @@ __global__ void __launch_bounds__(kThreads, 3) k_spmm(Ctx c) {
             cur = g;
         }
         const GraphDesc &sg = wd[warp];
-        const int K = sg.K;
         const int64_t base = (int64_t)blk * sg.rows_per_item;
-        BlockRow br;
-        const uint32_t sk = load_block_rows<true>(sg, base, sg.rows_per_item, lane, br);
-        for_sorted_rows(sg, base, sk, lane, [&](int64_t row, int gl, int lpr, int bi) {
-            const int64_t rs = __shfl_sync(0xffffffffu, br.rs, bi), re = __shfl_sync(0xffffffffu, br.re, bi);
-            int2 t;
-            t.x = __shfl_sync(0xffffffffu, br.tab.x, bi);
-            t.y = __shfl_sync(0xffffffffu, br.tab.y, bi);
-            const RowTail rt = row_tail(sg, t, __shfl_sync(0xffffffffu, br.dinv, bi));
-            if (K <= 1) light_row_reg<1>(sg, row, rs, re, rt, gl, lpr, err);
-            else if (K <= 2) light_row_reg<2>(sg, row, rs, re, rt, gl, lpr, err);
-            else if (K <= 4) light_row_reg<4>(sg, row, rs, re, rt, gl, lpr, err);
-            else if (K <= 8) light_row_reg<8>(sg, row, rs, re, rt, gl, lpr, err);
-            else light_row_smem(sg, row, rs, re, rt, gl, lpr, sacc, lane, err);
-        });
-        if (err) {
-            atomicOr(sg.status, err);
-            err = 0;
+        if (sg.val) spmm_block<V, true>(sg, base, sacc, ring, lane);
+        else spmm_block<V, false>(sg, base, sacc, ring, lane);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Re-embedding with new labels on the CSR a previous call built (Section 2: W from known or
+// predicted labels; the CSR, the degrees D and the hub and bucket plans do not depend on
+// the labels).  k_labels recounts n_k and checks the labels; its first thread also checks
+// that the workspace was built for this plan, and if not reports GEE_STATUS_STALE and
+// empties the hub and bucket work so that k_spmm only reads in-range memory.  k_nodetab
+// then rebuilds the node table s_j = D_jj^-1/2 / n_{y_j} from the stored D^-1/2.
+
+__global__ void __launch_bounds__(kThreads) k_labels(Ctx c) {
+    __shared__ uint32_t h[kMaxK];
+    __shared__ uint32_t s_err;
+    const GraphDesc &g = c.g0;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_err = 0;
+        if (blockIdx.x == 0 && __ldcg(&c.cb.cs->stamp) != g.stamp) {
+            atomicOr(g.status, kStStale);
+            c.cb.cs->hub_chunks = 0u;
+            c.cb.cs->light_items = 0u;
         }
     }
+    for (int i = tid; i < g.K; i += kThreads) h[i] = 0;
+    __syncthreads();
+    const int64_t n0 = (int64_t)blockIdx.x * kPrepTile;
+    const int n = (int)min64(kPrepTile, (int64_t)g.N - n0);
+    uint32_t err = 0;
+    for (int i = tid; i < n; i += kThreads) {
+        const int yv = __ldg(g.y + n0 + i);
+        if (yv < -1 || yv >= g.K) err |= kStLabel;
+        else if (yv >= 0) atomicAdd(&h[yv], 1u);
+    }
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    for (int i = tid; i < g.K; i += kThreads)
+        if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(g.nk) + i, h[i]);
+    if (tid == 0 && s_err) atomicOr(g.status, s_err);
+}
+
+__global__ void __launch_bounds__(kThreads) k_nodetab(Ctx c) {
+    const GraphDesc &g = c.g0;
+    const bool lap = (g.flags & kOptLap) != 0;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * kThreads) {
+        const int yv = __ldg(g.y + j);
+        int2 tv = make_int2(0, 0);
+        if (yv >= 0 && yv < g.K) {
+            const int ny = __ldcg(g.nk + yv);
+            const float dv = lap ? __ldcg(g.dinv + j) : 1.0f;
+            tv = make_int2(yv, __float_as_int(ny > 0 ? dv / (float)ny : 0.0f));
+        }
+        g.tab[j] = tv;
+    }
+}
+
+// A product on a workspace that must hold a build of this plan (a row shard): if its stamp
+// does not match, report GEE_STATUS_STALE and empty the hub and bucket work.
+__global__ void k_stamp(Ctx c) {
+    if (threadIdx.x == 0 && __ldcg(&c.cb.cs->stamp) != c.g0.stamp) {
+        atomicOr(c.g0.status, kStStale);
+        c.cb.cs->hub_chunks = 0u;
+        c.cb.cs->light_items = 0u;
+    }
+}
+
+cudaError_t launch_stamp_check(const Ctx &c, cudaStream_t st) {
+    k_stamp<<<1, 32, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nodetab(const Ctx &c, cudaStream_t st) {
+    const int64_t N = c.g0.N;
+    if (N <= 0) return cudaSuccess;
+    k_nodetab<<<(int)min64((N + kThreads - 1) / kThreads, 152 * 8), kThreads, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(const Ctx &c, cudaStream_t st) {
+    const int64_t N = c.g0.N;
+    if (N <= 0) return cudaSuccess;
+    k_labels<<<(int)((N + kPrepTile - 1) / kPrepTile), kThreads, 0, st>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_nodetab<<<(int)min64((N + kThreads - 1) / kThreads, 152 * 8), kThreads, 0, st>>>(c);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------
@@ -1754,9 +2186,18 @@ cudaError_t launch_wdeg(const Ctx &c, int blocks, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmm(const Ctx &c, int blocks, bool smem_acc, cudaStream_t st) {
+// shared memory of k_spmm: per warp a [kpad][32] float accumulator and rings of `ring`
+// 16-byte slots per lane for col (and val when `ringw`)
+size_t spmm_smem(int kpad, int ring, bool ringw) {
+    return (size_t)kWarps * ((size_t)kpad * 128 + (size_t)ring * 512 * (ringw ? 2 : 1));
+}
+
+cudaError_t launch_spmm(const Ctx &c, int blocks, int kpad, int ring, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    k_spmm<<<blocks, kThreads, smem_acc ? kSmemAccBytes : 0, st>>>(c);
+    const size_t sm = spmm_smem(kpad, ring, c.cb.ringw != 0);
+    if (ring >= 8) k_spmm<8><<<blocks, kThreads, sm, st>>>(c);
+    else if (ring >= 4) k_spmm<4><<<blocks, kThreads, sm, st>>>(c);
+    else k_spmm<2><<<blocks, kThreads, sm, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1777,7 +2218,12 @@ cudaError_t configure_kernels() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIdRingBytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAccBytes);
+    const int big_spmm = 200 * 1024;
+    e = cudaFuncSetAttribute(k_spmm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_spmm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_spmm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_spmm);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_spmm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big_spmm);
 }
 
 static int occ(const void *f, size_t smem) {
@@ -1786,7 +2232,10 @@ static int occ(const void *f, size_t smem) {
     return n > 0 ? n : 1;
 }
 
-int occupancy_spmm(bool smem_acc) { return occ((const void *)k_spmm, smem_acc ? kSmemAccBytes : 0); }
+int occupancy_spmm(int kpad, int ring, bool ringw) {
+    const void *f = ring >= 8 ? (const void *)k_spmm<8> : (ring >= 4 ? (const void *)k_spmm<4> : (const void *)k_spmm<2>);
+    return occ(f, spmm_smem(kpad, ring, ringw));
+}
 int occupancy_wdeg() { return occ((const void *)k_wdeg, 0); }
 
 }  // namespace gee

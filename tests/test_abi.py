@@ -121,9 +121,10 @@ def test_python_constants_match_header(tmp_path):
     import paper_2406_03726_gb300 as gee
     pairs = {"GEE_DIAG_AUG": gee.DIAG_AUG, "GEE_LAPLACIAN": gee.LAPLACIAN, "GEE_CORRELATION": gee.CORRELATION,
              "GEE_ALL_OPTIONS": gee.ALL_OPTIONS, "GEE_NO_GRAPH_CACHE": gee.NO_GRAPH_CACHE,
+             "GEE_SYMMETRIZE": gee.SYMMETRIZE,
              "GEE_STATUS_INDEX": gee.STATUS_INDEX, "GEE_STATUS_LABEL": gee.STATUS_LABEL,
              "GEE_STATUS_WEIGHT": gee.STATUS_WEIGHT, "GEE_STATUS_TIMEOUT": gee.STATUS_TIMEOUT,
-             "GEE_STATUS_INTERNAL": gee.STATUS_INTERNAL,
+             "GEE_STATUS_INTERNAL": gee.STATUS_INTERNAL, "GEE_STATUS_STALE": gee.STATUS_STALE,
              "GEE_ERR_NOMEM": gee.ERR_NOMEM, "GEE_PENDING": gee.PENDING, "GEE_ERR_STATE": gee.ERR_STATE,
              "GEE_MAX_N": gee.MAX_N, "GEE_MAX_E": gee.MAX_E, "GEE_MAX_K": gee.MAX_K,
              "GEE_NUM_PHASES": len(gee.PHASES)}
@@ -139,11 +140,35 @@ def test_kernel_constants_match_header(tmp_path):
     consts = {m[0]: int(m[1]) for m in re.findall(r"\b(k\w+) = (\d+)u?\b", hdr)}
     body = "".join(f'printf("{k} %lld\\n", (long long)({k}));\n' for k in
                    ("GEE_STATUS_INDEX", "GEE_STATUS_LABEL", "GEE_STATUS_WEIGHT", "GEE_STATUS_TIMEOUT",
-                    "GEE_STATUS_INTERNAL", "GEE_DIAG_AUG", "GEE_LAPLACIAN", "GEE_CORRELATION", "GEE_MAX_K"))
+                    "GEE_STATUS_INTERNAL", "GEE_STATUS_STALE", "GEE_DIAG_AUG", "GEE_LAPLACIAN", "GEE_CORRELATION", "GEE_MAX_K"))
     c = dict((k, int(v)) for k, v in (line.split() for line in _c_layout(tmp_path, body).splitlines()))
     assert (consts["kStIndex"], consts["kStLabel"], consts["kStWeight"], consts["kStTimeout"],
-            consts["kStInternal"]) == (c["GEE_STATUS_INDEX"], c["GEE_STATUS_LABEL"], c["GEE_STATUS_WEIGHT"],
-                                       c["GEE_STATUS_TIMEOUT"], c["GEE_STATUS_INTERNAL"])
+            consts["kStInternal"], consts["kStStale"]) == (c["GEE_STATUS_INDEX"], c["GEE_STATUS_LABEL"],
+                                                         c["GEE_STATUS_WEIGHT"], c["GEE_STATUS_TIMEOUT"],
+                                                         c["GEE_STATUS_INTERNAL"], c["GEE_STATUS_STALE"])
     assert (consts["kOptAug"], consts["kOptLap"], consts["kOptCor"]) == \
         (c["GEE_DIAG_AUG"], c["GEE_LAPLACIAN"], c["GEE_CORRELATION"])
     assert consts["kMaxK"] == c["GEE_MAX_K"]
+
+
+def test_tune_cache_file_roundtrip_on_the_host(lib, tmp_path):
+    # the file format needs no GPU: an empty cache saves as valid JSON; a file with entries of
+    # another GPU loads nothing (they stay in the file); malformed or missing files are refused
+    import json
+    import paper_2406_03726_gb300 as gee
+    assert gee.gee_tune_cache_clear() == 0
+    p = tmp_path / "tune.json"
+    assert gee.gee_tune_cache_save(p) == 0
+    assert json.loads(p.read_text()) == {"format": "gee-tune-1", "entries": []}
+    entry = ('{"gpu": "Some Other GPU", "E": 1000, "N": 100, "K": 3, "weighted": 1, '
+             '"fixed": [7, 0, 0, 0, 0, 0], "best": [7, 2048, 0, 4, 8, 64], "ms": 0.125}')
+    p.write_text('{"format": "gee-tune-1", "entries": [\n' + entry + '\n]}\n')
+    assert json.loads(p.read_text())["entries"][0]["best"] == [7, 2048, 0, 4, 8, 64]
+    assert gee.gee_tune_cache_load(p) == (0, 0)
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"format": "gee-tune-1", "entries": [\n{"gpu": "X", "E": oops}\n]}\n')
+    assert gee.gee_tune_cache_load(bad)[0] == 1
+    assert gee.gee_tune_cache_load(tmp_path / "missing.json")[0] == 1
+    nohead = tmp_path / "nohead.json"
+    nohead.write_text(entry + "\n")
+    assert gee.gee_tune_cache_load(nohead)[0] == 1

@@ -316,3 +316,29 @@ def test_row_parallel_oracle_larger_graphs_and_errors():
     bad[5] = g.N
     with pytest.raises(ValueError):
         oracle.embed_rows(g.src, bad, g.w, g.N, g.labels, g.K, 7, 4)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_symmetrize_is_the_concatenation_of_both_directions(seed):
+    # the undirected reading: every listed edge, then the reverse of every non-self-loop
+    g = random_tiny(seed, n_max=50, e_max=300, weighted=True)
+    s, d, w = oracle.symmetrize(g.src, g.dst, g.w)
+    m = g.src != g.dst
+    assert np.array_equal(s, np.concatenate([g.src, g.dst[m]]))
+    assert np.array_equal(d, np.concatenate([g.dst, g.src[m]]))
+    assert np.array_equal(w, np.concatenate([g.w, g.w[m]]))
+    s2, d2, w2 = oracle.symmetrize(g.src, g.dst, None)
+    assert np.array_equal(s2, s) and np.array_equal(d2, d) and w2 is None
+
+
+def test_symmetrized_one_direction_reproduces_the_undirected_graph():
+    # an SBM graph stores both directions; listing each undirected edge once (src < dst) and
+    # symmetrizing gives the same A, so the same Z up to summation order
+    g = sbm(400, seed=91, weighted=True)
+    one = g.src < g.dst
+    s, d, w = oracle.symmetrize(g.src[one], g.dst[one], g.w[one])
+    assert s.size == g.E
+    for f in ALL_FLAGS:
+        Z = oracle.embed_graph(g, f)
+        Zs = oracle.embed(s, d, w, g.N, g.labels, g.K, f)
+        assert np.allclose(Zs, Z, rtol=1e-12, atol=1e-15), f
