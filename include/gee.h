@@ -101,8 +101,8 @@ typedef struct gee_opts {
                               Z (a lane's entries are added in the same order) */
     int32_t short_len;     /* K > 8: light rows of at most this many entries are taken one lane
                               per row, longer ones by a whole warp: 8, 16, 32, 64, 128 or 256;
-                              0 = auto (64).  Changes the order of additions of the rows between
-                              the old and the new bound */
+                              0 = auto (256).  Changes the order of additions of the rows
+                              between the old and the new bound */
 } gee_opts;
 
 /*
@@ -231,8 +231,9 @@ int gee_embed_timed(const int32_t *d_src, const int32_t *d_dst, const float *d_w
  * (Section 3 CSR; Section 2 n_k and D).  Same inputs and workspace as gee_embed.
  *
  *   d_rowptr  device int32 [N+1]  index_pointers of A (rowptr[N] = E)
- *   d_col     device int32 [E]    col_indices, rows in input order
- *   d_val     device float32 [E]  data (1.0 for unweighted input), or NULL to skip
+ *   d_col     device int32 [E]    col_indices, rows in input order ([2E] with GEE_SYMMETRIZE)
+ *   d_val     device float32 [E]  data (1.0 for unweighted input), or NULL to skip ([2E] with
+ *                                 GEE_SYMMETRIZE)
  *   d_nk      device int32 [K]    class sizes n_k, or NULL
  *   d_deg     device float32 [N]  D_ii (row sum, +1 with GEE_DIAG_AUG), or NULL
  * Integer outputs are exact.  For unweighted input d_deg holds exact integers for every

@@ -167,9 +167,9 @@ class BatchPlan:
     """A reusable plan for many graphs (device tensors), launched as one kernel sequence
     (replayed as a CUDA graph with use_graph=True)."""
 
-    def __init__(self, graphs, flags=0, hub_threshold=0, lanes_per_row=0, device=None, stream=None):
+    def __init__(self, graphs, flags=0, hub_threshold=0, lanes_per_row=0, device=None, stream=None, opts=None):
         import torch
-        self.opts = make_opts(flags, hub_threshold, lanes_per_row)
+        self.opts = opts if opts is not None else make_opts(flags, hub_threshold, lanes_per_row)
         self.items = []
         self.Z = []
         for (src, dst, w, labels, N, K) in graphs:

@@ -175,7 +175,7 @@ void plan_params(const Shape &s, const gee_opts &o, bool want_deg, GraphDesc &d,
         d.rows_per_item = rpi;
     }
     d.wdeg = (s.weighted && ((d.flags & kOptLap) || want_deg)) ? 1 : 0;
-    d.short_len = o.short_len > 0 ? o.short_len : 64;
+    d.short_len = o.short_len > 0 ? o.short_len : 256;
     d.vec = o.vec_width;  // 0: chosen at launch from the shared memory it leaves
     // K > 8: capacities of the length buckets.  Bucket b >= 1 of the one-lane buckets
     // holds rows of more than lo_b entries (so at most E / (lo_b + 1) of them); the
@@ -264,8 +264,8 @@ int check_opts(const gee_opts &o) {
         (o.lanes_per_row & (o.lanes_per_row - 1)) || o.rows_per_item < 0 || o.rows_per_item > 32 ||
         (o.rows_per_item & (o.rows_per_item - 1)) ||
         !(o.vec_width == 0 || o.vec_width == 2 || o.vec_width == 4 || o.vec_width == 8) ||
-        !(o.short_len == 0 || o.short_len == 8 || o.short_len == 16 || o.short_len == 32 || o.short_len == 64 ||
-          o.short_len == 128 || o.short_len == 256))
+        !(o.short_len == 0 || (o.short_len >= 8 && o.short_len <= (4 << kWarpBucket) &&
+                               !(o.short_len & (o.short_len - 1)))))
         return GEE_ERR_ARG;
     return GEE_OK;
 }
@@ -957,12 +957,14 @@ TuneAxes tune_axes(const Shape &s, const gee_opts &o) {
     auto add = [](std::vector<int32_t> &v, int32_t x) {
         if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
     };
-    add(ax.vec, d.vec);
+    // an automatic ring depth is resolved: the tuner always returns an explicit one
     if (o.vec_width == 0)
         for (int32_t v : {8, 4, 2}) add(ax.vec, v);
+    else
+        add(ax.vec, d.vec);
     add(ax.shortl, d.short_len);
     if (o.short_len == 0 && s.K > kRegK)
-        for (int32_t v : {16, 32, 64, 128, 256}) add(ax.shortl, v);
+        for (int32_t v : {32, 64, 128}) add(ax.shortl, v);
     add(ax.hub, d.hub_C);
     if (o.hub_threshold == 0) {
         add(ax.hub, std::max(1024, d.hub_C / 2));
@@ -1279,15 +1281,16 @@ int gee_build_csr(const int32_t *d_src, const int32_t *d_dst, const float *d_w, 
     GEE_TRY(run_single(p, dev, st, nullptr, false));
     GEE_TRY(cuda_check(cudaMemcpyAsync(d_rowptr, d.rowptr, sizeof(int32_t) * ((size_t)N + 1),
                                        cudaMemcpyDeviceToDevice, st)));
-    if (E > 0) {
+    const int64_t cap = d.E;  // E, or 2E with GEE_SYMMETRIZE (rowptr[N] entries are used)
+    if (cap > 0) {
         GEE_TRY(cuda_check(
-            cudaMemcpyAsync(d_col, d.col, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToDevice, st)));
+            cudaMemcpyAsync(d_col, d.col, sizeof(int32_t) * (size_t)cap, cudaMemcpyDeviceToDevice, st)));
         if (d_val) {
             if (d.val)
                 GEE_TRY(cuda_check(
-                    cudaMemcpyAsync(d_val, d.val, sizeof(float) * (size_t)E, cudaMemcpyDeviceToDevice, st)));
+                    cudaMemcpyAsync(d_val, d.val, sizeof(float) * (size_t)cap, cudaMemcpyDeviceToDevice, st)));
             else
-                GEE_TRY(cuda_check(launch_fill(d_val, E, 1.0f, st)));
+                GEE_TRY(cuda_check(launch_fill(d_val, cap, 1.0f, st)));
         }
     }
     if (d_nk)

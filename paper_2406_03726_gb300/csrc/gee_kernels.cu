@@ -144,6 +144,13 @@ __device__ __forceinline__ uint32_t lanes_log2_for(int len) {
     return (uint32_t)min(5, 32 - __clz(len - 1) - 3);
 }
 
+// Length bucket of a light row of a K > 8 graph that is taken one lane per row: 0 for at
+// most 8 entries, b for (4 << b, 8 << b], capped at the last one-lane bucket.
+__device__ __forceinline__ int bucket_of(int len) {
+    if (len <= 8) return 0;
+    return min(kWarpBucket - 1, 32 - __clz(len - 1) - 3);
+}
+
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u; }
 
 // ------------------------------------------------------------------------------------
@@ -732,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
 
         // ---- per digit: warp offsets, tile counts, tile-local starts, global positions
         uint32_t tcount[8];  // counts of the owned digits (dpt <= 8)
-        uint32_t loc = 0;
+        uint32_t loc = 0, nranked = 0;  // nranked: the tile's ranked elements (dropped ones are not)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int d = dlo + j;
@@ -759,7 +766,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
             __syncthreads();  // S
             uint32_t tr = x - loc;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) tr += (w < warp) ? s_scan[w] : 0u;
+            for (int w = 0; w < kWarps; ++w) {
+                tr += (w < warp) ? s_scan[w] : 0u;
+                nranked += s_scan[w];
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int d = dlo + j;
@@ -793,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
         uint32_t *outk = FINAL ? reinterpret_cast<uint32_t *>(sg.col) : sg.tmpk;
         float *outw = FINAL ? sg.val : sg.tmpw;
 #pragma unroll 4
-        for (int s = tid; s < n; s += kThreads) {
+        for (int s = tid; s < (int)nranked; s += kThreads) {
             const uint32_t pos = spos[s];
             if (pos >= E32) {
                 err |= kStInternal;
@@ -1084,7 +1094,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
                     err |= kStInternal;  // capacity is sized so this cannot happen
                 }
             } else if (buckets) {
-                bks[k] = cnt > sg.short_len ? kWarpBucket : (int)lanes_log2_for(cnt);
+                bks[k] = cnt > sg.short_len ? kWarpBucket : bucket_of(cnt);
                 rk[k] = atomicAdd(&s_bcnt[bks[k]], 1u);  // rank within the CTA (order is free)
             }
             if (!sg.wdeg) write_node_known(sg, j, (float)cnt + aug, lap, yv[k], ny[k]);
@@ -1529,11 +1539,10 @@ struct RegAcc {
 template <int S, bool W, class A>
 __device__ __forceinline__ void stream_row(const GraphDesc &g, int rs, int re, int gl, int lpr, A &acc,
                                            const Ring &ring, int lane) {
-    static_assert(S >= 2 && (S & (S - 1)) == 0, "ring depth");
     const int step = 4 * lpr;
     const uint32_t nmax = (uint32_t)g.ncols - 1u;
     const int b0 = (rs & ~3) + 4 * gl;
-    const int nv = b0 < re ? (re - b0 + step - 1) / step : 0;  // vectors of this lane
+    const int nv = b0 < re ? (re - b0 + step - 1) / step : 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         if (s < nv) {
@@ -1542,53 +1551,36 @@ __device__ __forceinline__ void stream_row(const GraphDesc &g, int rs, int re, i
         }
         cp_async_commit();
     }
-    // two vectors per step: eight gathers in flight before the adds
-    for (int i = 0; i < nv; i += 2) {
-        cp_async_wait<S - 2>();  // the groups complete in order: vectors i and i + 1 have landed
-        int4 cv[2];
-        float4 wv[2];
-        int2 t[8];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int slot = 32 * ((i + u) & (S - 1)) + lane;
-            cv[u] = make_int4(0, 0, 0, 0);
-            wv[u] = make_float4(1.f, 1.f, 1.f, 1.f);
-            if (i + u < nv) {
-                cv[u] = ring.rc[slot];
-                if (W) wv[u] = ring.rv[slot];
-            }
-            t[4 * u] = __ldg(g.tab + min((uint32_t)cv[u].x, nmax));
-            t[4 * u + 1] = __ldg(g.tab + min((uint32_t)cv[u].y, nmax));
-            t[4 * u + 2] = __ldg(g.tab + min((uint32_t)cv[u].z, nmax));
-            t[4 * u + 3] = __ldg(g.tab + min((uint32_t)cv[u].w, nmax));
+    for (int i = 0; i < nv; ++i) {
+        cp_async_wait<S - 1>();
+        const int slot = 32 * (i & (S - 1)) + lane;
+        const int4 cv = ring.rc[slot];
+        float4 wv = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (W) wv = ring.rv[slot];
+        const int bi = b0 + i * step;
+        int2 t[4];
+        t[0] = __ldg(g.tab + min((uint32_t)cv.x, nmax));
+        t[1] = __ldg(g.tab + min((uint32_t)cv.y, nmax));
+        t[2] = __ldg(g.tab + min((uint32_t)cv.z, nmax));
+        t[3] = __ldg(g.tab + min((uint32_t)cv.w, nmax));
+        if (i + S < nv) {
+            cp_async16(ring.rc + slot, g.col + bi + S * step);
+            if (W) cp_async16(ring.rv + slot, g.val + bi + S * step);
         }
+        cp_async_commit();
+        const float ws[4] = {wv.x, wv.y, wv.z, wv.w};
+        if (bi >= rs && bi + 4 <= re) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int slot = 32 * ((i + u) & (S - 1)) + lane;
-            if (i + u + S < nv) {
-                cp_async16(ring.rc + slot, g.col + b0 + (i + u + S) * step);
-                if (W) cp_async16(ring.rv + slot, g.val + b0 + (i + u + S) * step);
+            for (int q = 0; q < 4; ++q) {
+                const float sj = __int_as_float(t[q].y);
+                acc.add(t[q].x, W ? ws[q] * sj : sj);
             }
-            cp_async_commit();
-        }
+        } else {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (i + u >= nv) break;
-            const int bi = b0 + (i + u) * step;
-            const float ws[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
-            if (bi >= rs && bi + 4 <= re) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float sj = __int_as_float(t[4 * u + q].y);
-                    acc.add(t[4 * u + q].x, W ? ws[q] * sj : sj);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float sj = __int_as_float(t[4 * u + q].y);
-                    const bool in = bi + q >= rs && bi + q < re;
-                    acc.add(t[4 * u + q].x, in ? (W ? ws[q] * sj : sj) : 0.0f);
-                }
+            for (int q = 0; q < 4; ++q) {
+                const float sj = __int_as_float(t[q].y);
+                const bool in = bi + q >= rs && bi + q < re;
+                acc.add(t[q].x, in ? (W ? ws[q] * sj : sj) : 0.0f);
             }
         }
     }
@@ -1962,12 +1954,7 @@ __global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(Ctx c
     const uint32_t nbucket = __ldcg(&c.cb.cs->light_items);
     const int nb = kBuckets * c.G;
     int cur = -1;
-    // the claim of a warp's next item is issued when it starts an item, so the atomic's
-    // round trip overlaps the work
-    uint32_t next_raw = 0;
-    for (uint32_t it = warp_first_item(); it < nbucket;
-         it = __shfl_sync(0xffffffffu, next_raw, 0) + gridDim.x * kWarps) {
-        if (lane == 0) next_raw = atomicAdd(&c.cb.cs->ctr[7], 1u);
+    for (uint32_t it = warp_first_item(); it < nbucket; it = warp_next_item(&c.cb.cs->ctr[7])) {
         int idx = 0;
         if (lane == 0) {  // largest idx with bitem[idx] <= it
             int lo = 0, hi = nb;
@@ -1992,9 +1979,7 @@ __global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(Ctx c
     }
     // blocks of consecutive light rows of the K <= 8 graphs
     cur = -1;
-    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items;
-         it = __shfl_sync(0xffffffffu, next_raw, 0) + gridDim.x * kWarps) {
-        if (lane == 0) next_raw = atomicAdd(&c.cb.cs->ctr[5], 1u);
+    for (uint32_t it = warp_first_item(); it < (uint32_t)c.items; it = warp_next_item(&c.cb.cs->ctr[5])) {
         int blk;
         const int g = warp_item_graph(c, it, blk);
         if (g != cur) {

@@ -73,6 +73,10 @@ def test_tuning_fields_checked_on_host(lib):
     for bad in (gee.make_opts(7, 0, 0, 3), gee.make_opts(7, 0, 0, 64), gee.make_opts(7, 0, 5, 0),
                 gee.make_opts(7, -1, 0, 0)):
         assert gee.gee_embed(1, 1, None, 4, 5, 1, 3, bad, 1, 1, 1 << 20) == 1
+    # ring depth 2, 4 or 8; short-row bound a power of two from 8 to 256 (0: automatic)
+    for bad in (gee.make_opts(7, 0, 0, 0, 3), gee.make_opts(7, 0, 0, 0, 16), gee.make_opts(7, 0, 0, 0, 0, 48),
+                gee.make_opts(7, 0, 0, 0, 0, 4), gee.make_opts(7, 0, 0, 0, 0, 512)):
+        assert gee.gee_embed(1, 1, None, 4, 5, 1, 3, bad, 1, 1, 1 << 20) == 1
     # the autotuner's workspace covers every candidate, so it is at least the plain one
     for E, N, K, w in ((11_124_844, 10_000, 3, True), (20_000_000, 600_000, 50, False), (100, 10, 2, True)):
         assert gee.gee_autotune_workspace_size(E, N, K, w) >= gee.gee_workspace_size(E, N, K, w)

@@ -121,3 +121,54 @@ def test_batch_of_one_graph(gee):
         torch.cuda.synchronize()
         assert np.array_equal(Zb.cpu().numpy(), gee.embed(s, d, w, g.N, y, g.K, ALL).cpu().numpy())
     plan.close()
+
+
+def test_batch_with_split_hub_rows_in_many_graphs(gee):
+    """A low split threshold makes hub rows in most graphs of the batch, so the hub chunks of
+    different graphs share the k_wdeg / k_spmm hub phase (chunk -> hub -> graph mapping)."""
+    from synth import chung_lu
+    graphs = [chung_lu(n, n * d, seed=110 + i, K=k, weighted=(i % 2 == 0), d_max=n // 2)
+              for i, (n, d, k) in enumerate([(3000, 20, 5), (8000, 12, 24), (5000, 30, 3), (12000, 10, 40),
+                                             (2000, 40, 8), (6000, 16, 64)])]
+    dg = [dev_graph(g) for g in graphs]
+    hub = 512
+    assert all(int((np.bincount(g.src, minlength=g.N) > hub).sum()) > 0 for g in graphs)
+    plan = gee.BatchPlan([(s, d, w, y, g.N, g.K) for (s, d, w, y), g in zip(dg, graphs)], ALL, hub_threshold=hub)
+    Zs = plan.launch(use_graph=False)
+    torch.cuda.synchronize()
+    assert int(plan.status.abs().sum().item()) == 0
+    for g, (s, d, w, y), Zb in zip(graphs, dg, Zs):
+        assert_z_matches(Zb.double().cpu().numpy(), oracle.embed_graph(g, ALL), what=g.name)
+        solo = gee.embed(s, d, w, g.N, y, g.K, ALL | gee.NO_GRAPH_CACHE, hub_threshold=hub)
+        torch.cuda.synchronize()
+        assert torch.equal(solo, Zb), g.name
+    plan.close()
+
+
+@pytest.mark.slow
+def test_full_4096_graph_batch_on_a_seeded_sample(gee):
+    """The whole 4,096-graph mix (about 3.5e9 directed edges) in one launch sequence; every
+    64th graph, the largest and the most skewed are checked against the oracle."""
+    from synth.torch_batch import batch_graph_torch
+    specs = batch_specs(4096, seed=4)
+    graphs = [batch_graph_torch(sp, "cuda") for sp in specs]
+    torch.cuda.synchronize()
+    plan = gee.BatchPlan([(s, d, w, y, sp["N"], sp["K"]) for (s, d, w, y), sp in zip(graphs, specs)], ALL)
+    Zs = plan.launch(use_graph=True)
+    torch.cuda.synchronize()
+    assert int(plan.status.abs().sum().item()) == 0
+    largest = max(range(len(specs)), key=lambda i: specs[i]["E"])
+    skew = []
+    for i, (s, d, w, y) in enumerate(graphs):
+        deg = torch.bincount(s.long(), minlength=specs[i]["N"])
+        skew.append(float(deg.max().item()) / max(1.0, float(deg.float().mean().item())))
+    skewed = int(np.argmax(skew))
+    sample = sorted(set(list(range(0, len(specs), 64)) + [largest, skewed]))
+    from synth.graphs import Graph
+    for i in sample:
+        s, d, w, y = (t.cpu().numpy() for t in graphs[i])
+        g = Graph(s, d, w, y, specs[i]["N"], specs[i]["K"])
+        assert_z_matches(Zs[i].double().cpu().numpy(), oracle.embed_graph(g, ALL), what=f"graph {i}")
+    plan.close()
+    del graphs, Zs
+    torch.cuda.empty_cache()

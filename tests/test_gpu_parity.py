@@ -297,3 +297,34 @@ def test_host_buffer_entry_point(gee):
     rc = gee.gee_embed_host(src, dst, w, E, N, y, K, opts, Z, ws, n, None, st)
     assert rc == 0 and st[0] == 0
     assert_z_matches(Z.double().numpy(), oracle.embed_graph(g, ALL), what="host entry point")
+
+
+@pytest.mark.slow
+def test_serving_large_graph_sampled_rows(gee):
+    """The large serving graph: Chung-Lu, N = 2M, 100M undirected edges (200M directed),
+    K = 16, weighted.  index_pointers bit-exact, unweighted-equivalent row lengths exact,
+    weighted degrees within 1e-6, and 10,000 sampled rows of Z against the oracle."""
+    from synth.torch_batch import batch_graph_torch
+    spec = {"index": -1, "N": 2_000_000, "m": 100_000_000, "E": 200_000_000, "K": 16, "kind": "chung_lu",
+            "seed": 77}
+    src, dst, w, y = batch_graph_torch(spec, "cuda")
+    N, K = spec["N"], spec["K"]
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rowptr, col, val, nk, deg = gee.build_csr(src, dst, w, N, y, K, ALL, status=st)
+    Z = gee.embed(src, dst, w, N, y, K, ALL, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    s, d, wv, yv = (t.cpu().numpy() for t in (src, dst, w, y))
+    del col, val
+    torch.cuda.empty_cache()
+    rp = np.concatenate([[0], np.cumsum(np.bincount(s, minlength=N))])
+    assert np.array_equal(rowptr.cpu().numpy().astype(np.int64), rp)
+    assert np.array_equal(nk.cpu().numpy(), oracle.label_counts(yv, K))
+    dref = oracle.degrees(s, wv, N, oracle.DIAG_AUG)
+    dg = deg.double().cpu().numpy()
+    assert np.max(np.abs(dg - dref) / dref) <= 1e-6
+    Zo = oracle.embed(s, d, wv, N, yv, K, ALL)
+    rows = np.random.default_rng(5).choice(N, 10_000, replace=False)
+    hubs = np.argsort(np.diff(rp))[-50:]                  # the longest rows (split across CTAs)
+    pick = np.unique(np.concatenate([rows, hubs]))
+    assert_z_matches(Z.double().cpu().numpy()[pick], Zo[pick], what="N=2M sampled rows")

@@ -93,3 +93,44 @@ def test_server_cancel_and_state_errors(gee):
     assert gee.gee_server_release(srv.handle, tickets[0]) == gee.ERR_STATE   # already released
     assert srv.stats()["bytes_in_use"] == 0
     srv.close()
+
+
+def test_server_replays_a_seeded_poisson_trace(gee):
+    """Requests arrive on a seeded Poisson trace while earlier ones run (pageable and pinned
+    host inputs mixed, a tight budget so admission waits for memory): every result equals
+    the same graph embedded alone, bit for bit."""
+    import threading
+    import time
+    graphs = mix(48, seed=53, n_range=(200, 20000), d_range=(5.0, 120.0))
+    rng = np.random.default_rng(54)
+    gaps = rng.exponential(0.002, len(graphs))           # about 500 requests per second
+    host = []
+    for i, g in enumerate(graphs):
+        if i % 2:  # pinned inputs for every second request
+            pin = [torch.from_numpy(a).pin_memory().numpy() for a in (g.src, g.dst, g.w, g.labels)]
+            host.append(tuple(pin))
+        else:
+            host.append((g.src, g.dst, g.w, g.labels))
+    need = max(8 * g.E * 4 + g.N * g.K * 4 for g in graphs)
+    srv = gee.Server(max(64 << 20, 6 * need), ALL, max_batch=16, streams=2)
+    tickets = [None] * len(graphs)
+
+    def submitter():
+        for i, (g, h) in enumerate(zip(graphs, host)):
+            time.sleep(gaps[i])
+            tickets[i] = srv.submit(h[0], h[1], h[2], h[3], g.N, g.K)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for i, g in enumerate(graphs):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        z, st, lat = srv.poll(tickets[i], wait=True)
+        assert st == 0
+        assert np.array_equal(srv.fetch(tickets[i]), solo(gee, g)), g.name
+        srv.release(tickets[i])
+    th.join()
+    s = srv.stats()
+    assert s["completed"] == len(graphs) and s["bytes_in_use"] == 0 and s["last_error"] == 0
+    assert s["peak_bytes_in_use"] <= s["pool_bytes"] and s["launches"] >= 2
+    srv.close()
