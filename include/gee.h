@@ -50,10 +50,11 @@ extern "C" {
 /* Input format, not an option of the method: the edge list is undirected and lists each
  * edge once.  Every listed edge (i, j, e) with i != j then adds e to both A_ij and A_ji (a
  * self-loop (i, i, e) adds e to A_ii once), without the caller storing both directions:
- * the reverse copies are made inside the CSR build, which reads the input arrays once per
- * radix pass.  In the CSR, row i lists the edges with source i in input order, then the
- * edges with target i (other than self-loops) in input order.  The CSR then holds up to 2E
- * entries (gee_build_csr: col/val need room for 2E; rowptr[N] is the count). */
+ * the reverse copies are made inside the CSR build, whose first radix pass reads the
+ * input arrays once for both directions.  In the CSR, row i lists the edges that touch i
+ * in input order: edge e = (i, j) gives the entry of column j and edge e = (j, i), j != i,
+ * the entry of column j, each at the position of e in the list.  The CSR then holds up to
+ * 2E entries (gee_build_csr: col/val need room for 2E; rowptr[N] is the count). */
 #define GEE_SYMMETRIZE 0x200u
 
 /* Supported sizes. */
@@ -314,6 +315,9 @@ int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, const float *d_
  * r1, K, weighted, opts and workspace; steps 3 and 5 read what step 1 left in the
  * workspace (step 5 checks it on the device, GEE_STATUS_STALE otherwise).  With the same
  * explicit tuning fields the rows' sums run exactly as in gee_embed of the whole graph.
+ * GEE_SYMMETRIZE is refused (GEE_ERR_ARG; the size query returns 0): the reverse copy of a
+ * rank's edge belongs to another rank's row, so each rank passes both directions of the
+ * edges of its own rows.
  *
  *   d_src, d_dst, d_w  device [E]: the rank's edges; every d_src[e] in [r0, r1), every
  *                      d_dst[e] a global id in [0, N) (else GEE_STATUS_INDEX)

@@ -82,7 +82,7 @@ def _ptr(a):
 
 def symmetrize(src, dst, w=None):
     """(src, dst, w) of the directed list of an undirected edge list given once per edge:
-    every edge in input order, then the reverse of every non-self-loop edge in input order."""
+    for every edge in input order, the edge and then (unless it is a self-loop) its reverse."""
     src, dst, w = _i32(src), _i32(dst), _f32(w)
     E = src.size
     os_, od = np.zeros(2 * E, np.int32), np.zeros(2 * E, np.int32)

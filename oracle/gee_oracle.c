@@ -64,10 +64,10 @@ int oracle_validate(const int32_t *src, const int32_t *dst, const float *w, int6
     return err;
 }
 
-/* An undirected edge list that lists each edge once, as the directed list of A: every
- * edge (i, j, e) in input order, then for every edge with i != j the reverse (j, i, e),
- * again in input order (a self-loop is one entry of A_ii).  out_* have room for 2E
- * entries; returns the number written.  w and out_w may be NULL (unweighted). */
+/* An undirected edge list that lists each edge once, as the directed list of A: for every
+ * edge (i, j, e) in input order, the entry (i, j, e) and then, if i != j, its reverse
+ * (j, i, e) (a self-loop is one entry of A_ii).  out_* have room for 2E entries; returns
+ * the number written.  w and out_w may be NULL (unweighted). */
 int64_t oracle_symmetrize(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t *out_src,
                           int32_t *out_dst, float *out_w) {
     int64_t n = 0;
@@ -76,8 +76,6 @@ int64_t oracle_symmetrize(const int32_t *src, const int32_t *dst, const float *w
         out_dst[n] = dst[e];
         if (w && out_w) out_w[n] = w[e];
         ++n;
-    }
-    for (int64_t e = 0; e < E; ++e) {
         if (src[e] == dst[e]) continue;
         out_src[n] = dst[e];
         out_dst[n] = src[e];

@@ -108,16 +108,11 @@ struct Shape {
     bool weighted;
 };
 
-// Ranges of range_tiles sort tiles, one scatter CTA each.  Symmetrizing: as many ranges
-// over the input read forward as over the input read reversed (no range mixes the two).
+// Ranges of range_tiles sort tiles, one scatter CTA each (over the 2 Ein virtual entries
+// when symmetrizing).
 void set_ranges(GraphDesc &d, int32_t range_tiles) {
     d.range_tiles = range_tiles;
-    if (d.sym) {
-        const int64_t half_tiles = (d.Ein + kSortTile - 1) / kSortTile;
-        d.ranges = 2 * (int32_t)((half_tiles + range_tiles - 1) / range_tiles);
-    } else {
-        d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
-    }
+    d.ranges = (d.tiles_e + d.range_tiles - 1) / d.range_tiles;
 }
 
 // Plan parameters of one graph.  Everything that decides the order of floating-point
@@ -817,6 +812,8 @@ int shard_plan(int64_t E, int32_t N, int32_t r0, int32_t r1, int32_t K, int weig
                size_t ws_bytes, SinglePlan &p) {
     GEE_TRY(check_shard(E, N, r0, r1, K));
     GEE_TRY(check_opts(o));
+    // the reverse copies of a rank's edges belong to other ranks' rows: not supported
+    if (o.flags & GEE_SYMMETRIZE) return GEE_ERR_ARG;
     const Shape s{E, r1 - r0, K, weighted != 0};
     plan_single(s, o, false, nullptr, p, N, r0);
     if (ws == nullptr && ws_bytes == 0) return GEE_OK;  // sizing only

@@ -228,26 +228,11 @@ __device__ __forceinline__ int range_len(const GraphDesc &g, int r) {
     return n > 0 ? (int)n : 0;
 }
 
-// Range r of the (virtual) edge list as read from the input arrays: first edge e0 of the
-// input, length n, and whether the range reads the reverse copies.  Without symmetrizing
-// the ranges cut the input; with it, the first half of the ranges cuts the input read
-// forward and the second half the same input read with source and target swapped (the
-// reverse copies come after every forward edge: the CSR keeps each row's forward edges in
-// input order, then its reverse ones).
-__device__ __forceinline__ void coo_range(const GraphDesc &g, int r, int64_t &e0, int &n, bool &rev) {
-    const int64_t L = (int64_t)g.range_tiles * kSortTile;
-    if (!g.sym) {
-        rev = false;
-        e0 = range_begin(g, r);
-        n = range_len(g, r);
-        return;
-    }
-    const int rh = g.ranges >> 1;
-    rev = r >= rh;
-    e0 = (int64_t)(rev ? r - rh : r) * L;
-    const int64_t m = min64(L, g.Ein - e0);
-    n = m > 0 ? (int)m : 0;
-}
+// With GEE_SYMMETRIZE the ranges cut the virtual list of 2 Ein entries in which input
+// edge e gives entry 2e (i -> j) and entry 2e + 1 (j -> i): the CSR keeps a row's entries
+// in that order.  vshift is 1 then: virtual entry v reads input edge v >> 1, so a range or
+// tile reads its input slice once for both directions.
+__device__ __forceinline__ int vshift(const GraphDesc &g) { return g.sym ? 1 : 0; }
 
 // Stream the ids [0, n) of p through f(value), CTA-wide, through shared memory: stages of
 // 2048 ids are filled by TMA bulk copies, kIdStages of them in flight, and each thread
@@ -337,18 +322,22 @@ __global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
         const uint32_t N = (uint32_t)sg.N, R0 = (uint32_t)sg.row0;
         const uint32_t m = (1u << b1) - 1u;
         uint32_t parity = 0;
-        int64_t e0;
-        int rn;
-        bool rev;
-        coo_range(sg, t, e0, rn, rev);
-        stream_ids_staged((rev ? sg.dst : sg.src) + e0, rn, ring, parity, err, [&](int v) {
+        const int sh = vshift(sg);
+        const int64_t e0 = range_begin(sg, t) >> sh;  // the range's slice of the input
+        const int rn = range_len(sg, t) >> sh;
+        auto count = [&](int v) {
             v = (int)((uint32_t)v - R0);
             if ((uint32_t)v >= N) {
                 err |= kStIndex;
                 v = 0;
             }
             atomicAdd(&hw[(uint32_t)v & m], 1u);
-        });
+        };
+        stream_ids_staged(sg.src + e0, rn, ring, parity, err, count);
+        if (sh) {  // the reverse entries' rows are the targets
+            __syncthreads();  // the ring is free again
+            stream_ids_staged(sg.dst + e0, rn, ring, parity, err, count);
+        }
         __syncthreads();
         uint32_t *out = sg.cnt1 + ((size_t)t << b1);
         for (int d = tid; d < D; d += kThreads) {
@@ -528,13 +517,14 @@ __host__ __device__ constexpr size_t scatter_smem_bytes(int D) {
 }
 
 template <bool FINAL>
-__device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e0, int n, bool rev, uint32_t *stage,
+// Stage n entries of the input from e0 (COO passes: src, dst and w; the final pass of a
+// 2-pass graph: the packed keys and weights) into shared memory, a multiple of 4 of them.
+__device__ __forceinline__ int scatter_issue_stage(const GraphDesc &g, int64_t e0, int n, uint32_t *stage,
                                                    uint64_t *bar) {
     const bool coo = !FINAL || g.npass == 1;
     const uint32_t bytes = (uint32_t)(n & ~3) * 4u;
-    const int32_t *sp = rev ? g.dst : g.src, *dp = rev ? g.src : g.dst;  // reverse copies: swapped
-    const void *p0 = coo ? (const void *)(sp + e0) : (const void *)(g.tmpk + e0);
-    const void *p1 = coo ? (const void *)(dp + e0) : nullptr;
+    const void *p0 = coo ? (const void *)(g.src + e0) : (const void *)(g.tmpk + e0);
+    const void *p1 = coo ? (const void *)(g.dst + e0) : nullptr;
     const void *p2 = g.w ? (coo ? (const void *)(g.w + e0) : (const void *)(g.tmpw + e0)) : nullptr;
     const bool ok = bytes > 0 && aligned16(p0) && (!p1 || aligned16(p1)) && (!p2 || aligned16(p2));
     if (ok) {
@@ -628,21 +618,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
 
     const int dpt = (D + kThreads - 1) / kThreads;
     const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
-    int64_t r0;
-    int rn;
-    bool rev = false;
-    if (coo) coo_range(sg, r, r0, rn, rev);
-    else {
-        r0 = range_begin(sg, r);
-        rn = range_len(sg, r);
-    }
+    // virtual entries of the range (a tile is kSortTile of them); with symmetrizing, the
+    // COO pass reads input edge v >> 1 for entry v
+    const int sh = coo ? vshift(sg) : 0;
+    const int64_t r0 = range_begin(sg, r);
+    const int rn = range_len(sg, r);
     const int ntiles = (rn + kSortTile - 1) / kSortTile;
     uint32_t err = 0;
 
     if (tid == 0) {
         s_err = 0;
         mbar_init(&bar, 1);
-        s_staged = scatter_issue_stage<FINAL>(sg, r0, min(rn, kSortTile), rev, stage, &bar);
+        s_staged = scatter_issue_stage<FINAL>(sg, r0 >> sh, min(rn, kSortTile) >> sh, stage, &bar);
     }
     for (int i = tid; i < kWarps * BD; i += kThreads) bins[i] = 0u;
     for (int d = dlo; d < dhi; ++d) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
@@ -659,22 +646,27 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
             parity ^= 1u;
         }
 
-        // ---- the 8 elements of this thread (stage, or global for the tail)
+        // ---- the 8 elements of this thread (stage, or global for the tail); entry idx of
+        // the tile reads input entry idx >> sh, and with symmetrizing the odd entries are
+        // the reverse copies (source and target swapped)
         uint32_t key[kSortItems], pay[kSortItems];
         float wv[kSortItems];
         const int wbase = warp * (32 * kSortItems);
+        const int64_t ein = e0 >> sh;
         if (staged && n == kSortTile) {
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i) {
                 const int idx = wbase + i * 32 + lane;
-                const uint32_t a = stage[idx];
-                const uint32_t b = coo ? stage[kStreamWords + idx] : 0u;
-                wv[i] = has_w ? __uint_as_float(stage[2 * kStreamWords + idx]) : 1.0f;
-                scatter_item<FINAL>(coo, rev, a, b, wv[i], N, R0, NC, lb, nb, nmask, dmask, has_w, lap, key[i],
-                                    pay[i], err);
+                const int j = idx >> sh;
+                const bool rev = (idx & sh) != 0;
+                const uint32_t a0 = stage[j];
+                const uint32_t b0 = coo ? stage[kStreamWords + j] : 0u;
+                wv[i] = has_w ? __uint_as_float(stage[2 * kStreamWords + j]) : 1.0f;
+                scatter_item<FINAL>(coo, rev, rev ? b0 : a0, rev ? a0 : b0, wv[i], N, R0, NC, lb, nb, nmask, dmask,
+                                    has_w, lap, key[i], pay[i], err);
             }
         } else {
-            const int nst = staged ? (n & ~3) : 0;
+            const int nst = staged ? ((n >> sh) & ~3) : 0;  // staged input entries
 #pragma unroll
             for (int i = 0; i < kSortItems; ++i) {
                 const int idx = wbase + i * 32 + lane;
@@ -682,23 +674,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
                 pay[i] = 0;
                 wv[i] = 1.0f;
                 if (idx < n) {
+                    const int j = idx >> sh;
+                    const bool rev = (idx & sh) != 0;
                     uint32_t a, b = 0;
                     float x = 1.0f;
-                    if (idx < nst) {
-                        a = stage[idx];
-                        if (coo) b = stage[kStreamWords + idx];
-                        if (has_w) x = __uint_as_float(stage[2 * kStreamWords + idx]);
+                    if (j < nst) {
+                        a = stage[j];
+                        if (coo) b = stage[kStreamWords + j];
+                        if (has_w) x = __uint_as_float(stage[2 * kStreamWords + j]);
                     } else if (coo) {
-                        a = (uint32_t)ld_stream((rev ? sg.dst : sg.src) + e0 + idx);
-                        b = (uint32_t)ld_stream((rev ? sg.src : sg.dst) + e0 + idx);
-                        if (has_w) x = ld_stream(sg.w + e0 + idx);
+                        a = (uint32_t)ld_stream(sg.src + ein + j);
+                        b = (uint32_t)ld_stream(sg.dst + ein + j);
+                        if (has_w) x = ld_stream(sg.w + ein + j);
                     } else {
-                        a = ld_stream(sg.tmpk + e0 + idx);
-                        if (has_w) x = ld_stream(sg.tmpw + e0 + idx);
+                        a = ld_stream(sg.tmpk + ein + j);
+                        if (has_w) x = ld_stream(sg.tmpw + ein + j);
                     }
                     wv[i] = x;
-                    scatter_item<FINAL>(coo, rev, a, b, x, N, R0, NC, lb, nb, nmask, dmask, has_w, lap, key[i], pay[i],
-                                        err);
+                    scatter_item<FINAL>(coo, rev, rev ? b : a, rev ? a : b, x, N, R0, NC, lb, nb, nmask, dmask, has_w,
+                                        lap, key[i], pay[i], err);
                 }
             }
         }
@@ -706,8 +700,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
 
         // ---- start streaming the next tile of this range
         if (tid == 0 && ti + 1 < ntiles)
-            s_staged = scatter_issue_stage<FINAL>(sg, e0 + kSortTile, min(kSortTile, rn - (ti + 1) * kSortTile),
-                                                  rev, stage, &bar);
+            s_staged = scatter_issue_stage<FINAL>(sg, (e0 + kSortTile) >> sh,
+                                                  min(kSortTile, rn - (ti + 1) * kSortTile) >> sh, stage, &bar);
 
         // ---- stable rank within the warp: peer masks, then a per-warp counter per digit
         for (int i = lane; i < D / 2; i += 32) reinterpret_cast<uint32_t *>(mycnt)[i] = 0u;

@@ -65,6 +65,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert gee.gee_embed(None, None, None, 0, 5, 1, 0, None, 1, None, 0) == 1                 # K = 0
     assert gee.gee_embed(None, None, None, 0, 1 << 22, 1, 3, None, 1, None, 0) == 2           # N too large
     assert gee.gee_class_counts(None, None, 5, None, 3, None) == 1
+    # row shards: the range must lie in [0, N], and undirected-once input is refused
+    assert gee.gee_shard_workspace_size(100, 50, 0, 20, 3, False, gee.make_opts(7)) > 0
+    assert gee.gee_shard_workspace_size(100, 50, 30, 20, 3, False, gee.make_opts(7)) == 0
+    assert gee.gee_shard_workspace_size(100, 50, 0, 51, 3, False, gee.make_opts(7)) == 0
+    assert gee.gee_shard_workspace_size(100, 50, 0, 20, 3, False, gee.make_opts(7 | gee.SYMMETRIZE)) == 0
 
 
 def test_tuning_fields_checked_on_host(lib):

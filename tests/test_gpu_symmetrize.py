@@ -1,7 +1,7 @@
 """GEE_SYMMETRIZE: an undirected edge list given once per edge.  The reverse copies are
 made inside the CSR build; the CSR must equal, bit for bit, the oracle's CSR of the
-expanded list (every edge in input order, then the reverse of every non-self-loop edge in
-input order), and Z must match the oracle on that list."""
+expanded list (every edge in input order, each followed by its reverse unless it is a
+self-loop), and Z must match the oracle on that list."""
 import numpy as np
 import pytest
 
@@ -85,3 +85,13 @@ def test_symmetrize_reports_a_bad_target_read_as_a_source():
               status=st)
     torch.cuda.synchronize()
     assert int(st.item()) & gee.STATUS_INDEX
+
+
+@pytest.mark.slow
+def test_symmetrize_chung_lu_600k_given_once():
+    """The Chung-Lu N=600,000 graph (10M undirected edges, K=50) given once per edge: the
+    CSR of its 20M entries bit for bit, and Z with every option against the oracle."""
+    import paper_2406_03726_gb300 as gee
+    g = _one_direction(chung_lu(600_000, 10_000_000, seed=3))
+    assert g.E == 10_000_000
+    _check(gee, g, (ALL,))

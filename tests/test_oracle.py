@@ -319,15 +319,18 @@ def test_row_parallel_oracle_larger_graphs_and_errors():
 
 
 @pytest.mark.parametrize("seed", range(10))
-def test_symmetrize_is_the_concatenation_of_both_directions(seed):
-    # the undirected reading: every listed edge, then the reverse of every non-self-loop
+def test_symmetrize_interleaves_both_directions(seed):
+    # the undirected reading: every listed edge followed by its reverse, except for self-loops
     g = random_tiny(seed, n_max=50, e_max=300, weighted=True)
-    s, d, w = oracle.symmetrize(g.src, g.dst, g.w)
-    m = g.src != g.dst
-    assert np.array_equal(s, np.concatenate([g.src, g.dst[m]]))
-    assert np.array_equal(d, np.concatenate([g.dst, g.src[m]]))
-    assert np.array_equal(w, np.concatenate([g.w, g.w[m]]))
-    s2, d2, w2 = oracle.symmetrize(g.src, g.dst, None)
+    src, dst = np.append(g.src, [0, 0]).astype(np.int32), np.append(g.dst, [0, 1]).astype(np.int32)
+    wt = np.append(g.w, [0.5, 0.25]).astype(np.float32)   # a self-loop and an edge, last
+    s, d, w = oracle.symmetrize(src, dst, wt)
+    keep = np.stack([np.ones(src.size, bool), src != dst], 1).reshape(-1)
+    assert np.array_equal(s, np.stack([src, dst], 1).reshape(-1)[keep])
+    assert np.array_equal(d, np.stack([dst, src], 1).reshape(-1)[keep])
+    assert np.array_equal(w, np.stack([wt, wt], 1).reshape(-1)[keep])
+    assert list(s[-3:]) == [0, 0, 1] and list(d[-3:]) == [0, 1, 0]
+    s2, d2, w2 = oracle.symmetrize(src, dst, None)
     assert np.array_equal(s2, s) and np.array_equal(d2, d) and w2 is None
 
 
