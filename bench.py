@@ -617,7 +617,7 @@ def measure_single(gee, g, dev, steps, warmup, workload, barrier=None):
     e2e = e2e_measure(gee, g, dev, stream, opts, steps)
     launches = int(sum(1 for i, n in enumerate(names) if phase_cnt[i] > 0 and n != "memset"))  # per step
     out = {"value": E / (ms_per_step * 1e-3), "unit": UNIT, "ms_per_step": ms_per_step, "steps": steps,
-           "total_ms": total_ms, "workload": WORKLOADS[workload]["desc"], "N": N, "E": E, "K": K,
+           "opts": opts, "total_ms": total_ms, "workload": WORKLOADS[workload]["desc"], "N": N, "E": E, "K": K,
            "tuning": tuned, "roofline": roofline, "e2e": e2e, "gpu_launches_per_step": launches,
            "l2": "flushed before every step (256 MiB write, untimed)"}
     if hot_ms is not None:
@@ -631,6 +631,70 @@ def measure_single(gee, g, dev, steps, warmup, workload, barrier=None):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return out
+
+
+def measure_symmetrize(gee, g, dev, steps, opts):
+    """The same graph given once per undirected edge (the entries with source < target)
+    with GEE_SYMMETRIZE: the CSR build makes the reverse copies.  L2-flushed CUDA-event
+    steps, kernel times from gee_embed_timed, and the host-buffer path (half the input)."""
+    import torch
+    from synth.graphs import Graph
+    one = g.src < g.dst
+    h = Graph(g.src[one], g.dst[one], None if g.w is None else g.w[one], g.labels, g.N, g.K)
+    E_in, N, K = h.E, h.N, h.K
+    o = gee.make_opts(ALL_OPTIONS | gee.SYMMETRIZE, opts.hub_threshold, opts.lanes_per_row, opts.rows_per_item,
+                      opts.vec_width, opts.short_len)
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    src, dst, w, y = t(h.src), t(h.dst), t(h.w), t(h.labels)
+    nbytes = gee.gee_workspace_size(E_in, N, K, w is not None, o)
+    wsb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    Z = torch.empty((N, K), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    phase = np.zeros(gee_phase_count(), np.float32)
+    for _ in range(3):
+        gee.gee_embed(src, dst, w, E_in, N, y, K, o, Z, wsb, nbytes, stream, status)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        rc = gee.gee_embed(src, dst, w, E_in, N, y, K, o, Z, wsb, nbytes, stream, status)
+        ev[i][1].record(stream)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+    torch.cuda.synchronize()
+    acc, cnt = np.zeros_like(phase), np.zeros_like(phase)
+    for i in range(min(steps, KERNEL_TIMING_STEPS)):
+        flush.fill_(float(i))
+        gee.gee_embed_timed(src, dst, w, E_in, N, y, K, o, Z, wsb, nbytes, stream, status, phase)
+        acc[phase >= 0] += phase[phase >= 0]
+        cnt[phase >= 0] += 1
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} with GEE_SYMMETRIZE")
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    names = gee.PHASES
+    kern = {names[i]: round(float(acc[i] / cnt[i]), 5) for i in range(len(names))
+            if cnt[i] > 0 and names[i] != "memset" and acc[i] > 0}
+    E_csr = g.E  # entries of A: both directions of every undirected edge (no self-loops here)
+    wt = 1 if h.w is not None else 0
+    first = E_in * (8 + 4 * wt) + E_csr * (4 + 4 * wt)  # input read once, both copies written
+    peaks = load_peaks()
+    e2e = e2e_measure(gee, h, dev, stream, o, steps)
+    e2e["value"] = E_csr * e2e["value"] / E_in       # the metric counts entries of A
+    del src, dst, w, y, wsb, Z, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"ms_per_step": round(ms, 5), "value": E_csr / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "input_edges": E_in, "csr_entries": E_csr, "kernels_ms": kern,
+            "k_scatter_first": {"alg_bytes": int(first), "frac": round(first / (kern["k_scatter_first"] * 1e-3) / 1e9 /
+                                                                      peaks["hbm_gbs"], 4)},
+            "e2e": e2e,
+            "note": "the graph given once per undirected edge with GEE_SYMMETRIZE (same tuning fields); "
+                    "value counts the entries of A; the first radix pass reads the input once for both "
+                    "directions"}
 
 
 def e2e_alg_bytes(g):
@@ -666,6 +730,7 @@ def gpu_arm(args):
                 if name != args.workload:
                     subs[name] = measure_single(gee, make_graph(name), dev, min(args.steps, SUB_STEPS),
                                                 args.warmup, name)
+                    subs[name].pop("opts")
             subs["batch"] = measure_batch(gee, dev, args.batch_graphs, 3, 3)
             subs["serving"] = measure_serving(gee, dev, 200, SERVE_REPS)
     total_ms, E_job = m["total_ms"], g.E
@@ -685,6 +750,9 @@ def gpu_arm(args):
     if "hot_l2" in m:
         line["hot_l2"] = m["hot_l2"]
     line["reembed"] = m["reembed"]
+    if ws_n == 1 and not args.no_sub and args.workload == "cl600k":
+        line["symmetrize"] = measure_symmetrize(gee, g, dev, min(args.steps, SUB_STEPS), m.pop("opts"))
+    m.pop("opts", None)
     if subs:
         line["configs"] = subs
     if rank == 0:

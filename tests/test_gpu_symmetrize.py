@@ -95,3 +95,21 @@ def test_symmetrize_chung_lu_600k_given_once():
     g = _one_direction(chung_lu(600_000, 10_000_000, seed=3))
     assert g.E == 10_000_000
     _check(gee, g, (ALL,))
+
+
+def test_symmetrize_through_host_buffers():
+    """gee_embed_host with GEE_SYMMETRIZE: the host copies carry the edges once."""
+    import torch
+    import paper_2406_03726_gb300 as gee
+    g = _one_direction(sbm(3000, seed=7, weighted=True))
+    gs = type(g)(*oracle.symmetrize(g.src, g.dst, g.w), g.labels, g.N, g.K)
+    opts = gee.make_opts(ALL | gee.SYMMETRIZE)
+    n = gee.gee_host_workspace_size(g.E, g.N, g.K, True, opts)
+    assert n > gee.gee_host_workspace_size(g.E, g.N, g.K, True, gee.make_opts(ALL))   # room for 2E entries
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    Z = torch.empty((g.N, g.K), dtype=torch.float32).pin_memory()
+    st = np.zeros(1, np.uint32)
+    rc = gee.gee_embed_host(pin(g.src), pin(g.dst), pin(g.w), g.E, g.N, pin(g.labels), g.K, opts, Z, ws, n, None, st)
+    assert rc == 0 and st[0] == 0
+    assert_z_matches(Z.double().numpy(), oracle.embed_graph(gs, ALL), what="host entry point, symmetrized")
