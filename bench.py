@@ -484,7 +484,7 @@ def serve_arm(args, ws_n, rank, local, dev):
     return 0
 
 
-def measure_single(gee, g, dev, steps, warmup, workload, barrier=None):
+def measure_single(gee, g, dev, steps, warmup, workload, barrier=None, fixed=None):
     """One graph: autotuned options, `steps` L2-flushed CUDA-event-timed gee_embed calls,
     per-kernel times of gee_embed_timed calls right after, hot-L2 calls and the end-to-end
     host-buffer path.  Returns the record (no cross-rank reduction)."""
@@ -492,11 +492,14 @@ def measure_single(gee, g, dev, steps, warmup, workload, barrier=None):
     E, N, K = g.E, g.N, g.K
     t = lambda a: None if a is None else torch.from_numpy(a).to(dev)
     src, dst, w, y = t(g.src), t(g.dst), t(g.w), t(g.labels)
-    # the project's autotuner picks the split threshold and rows per work item for this
-    # graph (outside the timed region; it times candidate calls itself)
-    opts, tune_ms = gee.autotune(src, dst, w, N, y, K, ALL_OPTIONS)
+    # the project's autotuner picks the tuning fields for this graph (outside the timed
+    # region; it times candidate calls itself), unless they are given (profiling runs)
+    if fixed is None:
+        opts, tune_ms = gee.autotune(src, dst, w, N, y, K, ALL_OPTIONS)
+    else:
+        opts, tune_ms = gee.make_opts(ALL_OPTIONS, fixed[0], 0, fixed[1], fixed[2], fixed[3]), 0.0
     tuned = {"hub_threshold": int(opts.hub_threshold), "rows_per_item": int(opts.rows_per_item),
-             "autotune_ms_per_call": round(tune_ms, 4)}
+             "autotune_ms_per_call": round(tune_ms, 4), "source": "autotune" if fixed is None else "--opts"}
     for f in ("vec_width", "short_len"):
         if hasattr(opts, f):
             tuned[f] = int(getattr(opts, f))
@@ -723,7 +726,8 @@ def gpu_arm(args):
     barrier = torch.distributed.barrier if ws_n > 1 else None
     subs = {}
     with ClockSampler(local) as clk:
-        m = measure_single(gee, g, dev, args.steps, args.warmup, args.workload, barrier)
+        fixed = tuple(int(x) for x in args.opts.split(",")) if args.opts else None
+        m = measure_single(gee, g, dev, args.steps, args.warmup, args.workload, barrier, fixed)
         # the other workloads as sub-records (one GPU, default run)
         if ws_n == 1 and not args.no_sub:
             for name in ("sbm10k", "sbm2k"):
@@ -831,6 +835,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the sub-records of the other workloads")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--opts", default="", help="hub_threshold,rows_per_item,vec_width,short_len for the main "
+                                                "workload instead of the autotuner (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.workload in ("batch", "serve"):

@@ -97,9 +97,10 @@ typedef struct gee_opts {
                               mean degree): sets the automatic threshold (256 x lanes) */
     int32_t rows_per_item; /* light rows a warp claims at once: 1,2,4,...,32; 0 = auto */
     int32_t vec_width;     /* 16-byte vectors of col (and data) each lane of the product kernel
-                              keeps in flight: 2, 4 or 8; 0 = auto (8, fewer if shared memory
-                              would hold less than two CTAs per SM).  Never changes the bits of
-                              Z (a lane's entries are added in the same order) */
+                              keeps in flight: 2, 4 or 8; 0 = auto (the depth that keeps two or
+                              more CTAs per SM with the least shared memory, leaving the most L1
+                              for the node-table gathers).  Never changes the bits of Z (a
+                              lane's entries are added in the same order) */
     int32_t short_len;     /* K > 8: light rows of at most this many entries are taken one lane
                               per row, longer ones by a whole warp: 8, 16, 32, 64, 128 or 256;
                               0 = auto (256).  Changes the order of additions of the rows

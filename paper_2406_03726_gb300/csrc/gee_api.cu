@@ -38,6 +38,7 @@ cudaError_t launch_nodetab(const Ctx &c, cudaStream_t st);
 cudaError_t launch_stamp_check(const Ctx &c, cudaStream_t st);
 cudaError_t configure_kernels();
 int occupancy_spmm(int kpad, int ring, bool ringw);
+size_t spmm_smem(int kpad, int ring, bool ringw);
 int occupancy_wdeg();
 
 namespace {
@@ -376,11 +377,25 @@ cudaError_t launch_product(const LaunchPlan &lp, const DeviceInfo &dev, const Ct
     const int64_t hub_grid_max = cb.hub_cap > 0 ? cb.chunk_cap : 0;
     const int kpad = std::min(kMaxK, (std::max(1, cb.kmax) + 7) & ~7);
     const int wi = cb.ringw ? 1 : 0;
-    // ring depth: the requested one (automatic: 8), made shallower while fewer than two
-    // CTAs of the kernel would fit on an SM
-    int ring = lp.vec > 0 ? lp.vec : 8;
+    // ring depth: the requested one, or automatically the depth that keeps at least two
+    // CTAs per SM while their shared memory takes the least of the SM (the rest is L1,
+    // which caches the node-table gathers: on a power-law graph, three CTAs with a small
+    // L1 ran slower than two with a large one); ties go to the deeper ring
     auto occ_of = [&](int r) { return dev.occ_spmm[r >= 8 ? 2 : (r >= 4 ? 1 : 0)][kpad / 8 - 1][wi]; };
-    while (ring > 2 && occ_of(ring) < 2) ring >>= 1;
+    int ring = lp.vec;
+    if (ring <= 0) {
+        ring = 2;
+        size_t best = SIZE_MAX;
+        for (int r = 2; r <= 8; r <<= 1) {
+            const int o = occ_of(r);
+            if (o < 2) continue;
+            const size_t used = (size_t)o * spmm_smem(kpad, r, wi != 0);
+            if (used <= best) {
+                best = used;
+                ring = r;
+            }
+        }
+    }
     const int socc = std::max(1, occ_of(ring));
     const int64_t row_items = lp.items[kPfxRows];
     int64_t sneed = std::max<int64_t>(std::min<int64_t>(hub_grid_max, 2 * (int64_t)dev.sms),
