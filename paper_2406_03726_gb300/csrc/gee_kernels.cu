@@ -82,28 +82,45 @@ __device__ __forceinline__ int find_graph(const int32_t *prefix, int G, int item
     return lo;
 }
 
-// Copy graph g's descriptor to shared memory (thread 0 resolves the item) and return the
+// Copy graph g's descriptor to `dst` (shared memory), 4 bytes per lane of the calling warp:
+// from the batch's array in global memory, or for one graph from the kernel parameter
+// (every kernel takes its Ctx as a __grid_constant__ parameter, so it is read in place).
+// A one-thread struct copy of the ~400-byte descriptor spilled registers in every kernel.
+__device__ __forceinline__ void copy_desc(const Ctx &c, int g, GraphDesc *dst, int lane) {
+    constexpr int kWords = (int)(sizeof(GraphDesc) / 4);
+    static_assert(sizeof(GraphDesc) % 4 == 0, "descriptor words");
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    if (c.G > 1) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(c.graphs + g);
+        for (int i = lane; i < kWords; i += 32) d[i] = __ldg(src + i);
+    } else {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&c.g0);
+        for (int i = lane; i < kWords; i += 32) d[i] = src[i];
+    }
+}
+
+// Copy graph g's descriptor to shared memory (warp 0 resolves the item) and return the
 // item's index local to that graph.  Contains __syncthreads.
 __device__ __forceinline__ int load_desc(const Ctx &c, int item, GraphDesc *sg, int *sl,
                                          const int32_t *prefix) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int g = 0, base = 0;
         if (c.G > 1) {
             g = find_graph(prefix, c.G, item);
             base = __ldg(prefix + g);
-            *sg = c.graphs[g];
-        } else {
-            *sg = c.g0;
         }
-        sl[0] = item - base;
-        sl[1] = g;
+        copy_desc(c, g, sg, threadIdx.x);
+        if (threadIdx.x == 0) {
+            sl[0] = item - base;
+            sl[1] = g;
+        }
     }
     __syncthreads();
     return sl[0];
 }
 
 __device__ __forceinline__ void load_desc_idx(const Ctx &c, int g, GraphDesc *sg) {
-    if (threadIdx.x == 0) *sg = (c.G > 1) ? c.graphs[g] : c.g0;
+    if (threadIdx.x < 32) copy_desc(c, g, sg, threadIdx.x);
     __syncthreads();
 }
 
@@ -298,7 +315,7 @@ __device__ __forceinline__ void stream_ids_staged(const int32_t *p, int n, const
     if (tid < n - nb) f(ld_stream(p + nb + tid));
 }
 
-__global__ void __launch_bounds__(kThreads) k_prep(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_prep(const __grid_constant__ Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
     __shared__ uint32_t h[kWarps * kPrivDigits];
@@ -377,7 +394,7 @@ constexpr int kOffThreads = 1024;
 constexpr int kOffWarps = kOffThreads / 32;
 
 template <bool SECOND>
-__global__ void __launch_bounds__(kOffThreads) k_offsets(Ctx c) {
+__global__ void __launch_bounds__(kOffThreads) k_offsets(const __grid_constant__ Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
     __shared__ uint32_t s_red[kOffWarps];
@@ -575,7 +592,7 @@ __device__ __forceinline__ void scatter_item(bool coo, bool rev, uint32_t a, uin
 }
 
 template <bool FINAL>
-__global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
+__global__ void __launch_bounds__(kThreads, 4) k_scatter(const __grid_constant__ Ctx c) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
@@ -817,7 +834,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(Ctx c) {
 // by first-pass digit lo (bucket bases = the offsets of range 0 in cnt1), so the range
 // splits into segments of constant lo; within a segment the row of an element is
 // (hi << lbits) | lo.
-__global__ void __launch_bounds__(kThreads) k_count(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_count(const __grid_constant__ Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
     __shared__ uint32_t acc[kMaxDigits];
@@ -1008,7 +1025,7 @@ __device__ void bucket_item_prefix(const Ctx &c, uint32_t *s_scan) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_rowscan(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_rowscan(const __grid_constant__ Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
     __shared__ uint32_t s_scan[kWarps];
@@ -1152,14 +1169,7 @@ __device__ __forceinline__ int cta_next_item(uint32_t *ctr, int *s_it) { return 
 
 // Copy graph g's descriptor into this warp's shared slot.
 __device__ __forceinline__ void warp_load_desc(const Ctx &c, int g, GraphDesc *slot) {
-    const int lane = threadIdx.x & 31;
-    if (c.G > 1) {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(c.graphs + g);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(slot);
-        for (int i = lane; i < (int)(sizeof(GraphDesc) / 4); i += 32) dst[i] = __ldg(src + i);
-    } else if (lane == 0) {
-        *slot = c.g0;
-    }
+    copy_desc(c, g, slot, threadIdx.x & 31);
     __syncwarp();
 }
 
@@ -1295,7 +1305,7 @@ __device__ __forceinline__ void for_sorted_rows(const GraphDesc &g, int64_t base
 //              row sums the partials in chunk order
 //   light rows then each warp claims row blocks: a group of lanes per row, 16-byte
 //              loads, Neumaier-compensated FP32 per lane, deterministic two-sum tree
-__global__ void __launch_bounds__(kThreads) k_wdeg(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_wdeg(const __grid_constant__ Ctx c) {
     __shared__ GraphDesc sg;
     __shared__ int s_it;
     __shared__ double s_red[kThreads];
@@ -1907,7 +1917,7 @@ struct SpmmOcc {
 };
 
 template <int V>
-__global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(Ctx c) {
+__global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(const __grid_constant__ Ctx c) {
     extern __shared__ __align__(16) unsigned char spmm_smem_all[];
     __shared__ GraphDesc sg;
     __shared__ int s_it;
@@ -1996,7 +2006,7 @@ __global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(Ctx c
 // empties the hub and bucket work so that k_spmm only reads in-range memory.  k_nodetab
 // then rebuilds the node table s_j = D_jj^-1/2 / n_{y_j} from the stored D^-1/2.
 
-__global__ void __launch_bounds__(kThreads) k_labels(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_labels(const __grid_constant__ Ctx c) {
     __shared__ uint32_t h[kMaxK];
     __shared__ uint32_t s_err;
     const GraphDesc &g = c.g0;
@@ -2026,7 +2036,7 @@ __global__ void __launch_bounds__(kThreads) k_labels(Ctx c) {
     if (tid == 0 && s_err) atomicOr(g.status, s_err);
 }
 
-__global__ void __launch_bounds__(kThreads) k_nodetab(Ctx c) {
+__global__ void __launch_bounds__(kThreads) k_nodetab(const __grid_constant__ Ctx c) {
     const GraphDesc &g = c.g0;
     const bool lap = (g.flags & kOptLap) != 0;
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * kThreads) {
@@ -2043,7 +2053,7 @@ __global__ void __launch_bounds__(kThreads) k_nodetab(Ctx c) {
 
 // A product on a workspace that must hold a build of this plan (a row shard): if its stamp
 // does not match, report GEE_STATUS_STALE and empty the hub and bucket work.
-__global__ void k_stamp(Ctx c) {
+__global__ void k_stamp(const __grid_constant__ Ctx c) {
     if (threadIdx.x == 0 && __ldcg(&c.cb.cs->stamp) != c.g0.stamp) {
         atomicOr(c.g0.status, kStStale);
         c.cb.cs->hub_chunks = 0u;
