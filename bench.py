@@ -700,6 +700,54 @@ def measure_symmetrize(gee, g, dev, steps, opts):
                     "directions"}
 
 
+def measure_sparse(gee, g, dev, steps, K):
+    """Sparse Z (gee_embed_sparse) of the graph with its labels redrawn from K classes
+    (every fifth node unlabelled, seed 137): L2-flushed CUDA-event-timed calls."""
+    import torch
+    rng = np.random.default_rng(137)
+    y_np = rng.integers(0, K, g.N).astype(np.int32)
+    y_np[::5] = -1
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    src, dst, w, y = t(g.src), t(g.dst), t(g.w), t(y_np)
+    o = gee.make_opts(ALL_OPTIONS)
+    n = gee.gee_sparse_workspace_size(g.E, g.N, K, w is not None, o)
+    ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    cap = g.E + g.N
+    zr = torch.empty(g.N + 1, dtype=torch.int32, device=dev)
+    zc = torch.empty(cap, dtype=torch.int32, device=dev)
+    zv = torch.empty(cap, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def call():
+        rc = gee.gee_embed_sparse(src, dst, w, g.E, g.N, y, K, o, zr, zc, zv, cap, ws, n, stream, status)
+        if rc:
+            raise RuntimeError(gee.gee_strerror(rc))
+
+    for _ in range(3):
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        call()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"device status {int(status.item())} in gee_embed_sparse")
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    nnz = int(zr[g.N].item())
+    del src, dst, w, y, ws, zr, zc, zv, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"K": K, "ms_per_call": round(ms, 4), "value": g.E / (ms * 1e-3), "unit": UNIT, "nnz": nnz,
+            "dense_z_bytes": 4 * g.N * K, "sparse_z_bytes": 8 * nnz + 4 * (g.N + 1), "calls": steps,
+            "note": "gee_embed_sparse: CSR build, then Z as CSR over classes (labels redrawn from K classes, "
+                    "every fifth node unlabelled); L2 flushed before each call"}
+
+
 def e2e_alg_bytes(g):
     """Algorithmic bytes of a whole step from the edge list: the COO read once, the CSR
     written once, and the product's bytes."""
@@ -756,6 +804,7 @@ def gpu_arm(args):
     line["reembed"] = m["reembed"]
     if ws_n == 1 and not args.no_sub and args.workload == "cl600k":
         line["symmetrize"] = measure_symmetrize(gee, g, dev, min(args.steps, SUB_STEPS), m.pop("opts"))
+        line["sparse"] = [measure_sparse(gee, g, dev, 20, K) for K in (g.K, 100_000)]
     m.pop("opts", None)
     if subs:
         line["configs"] = subs

@@ -302,6 +302,34 @@ int gee_embed_static(const int32_t *d_src, const int32_t *d_dst, const float *d_
                      uint32_t *d_status);
 
 /* ------------------------------------------------------------------------------------
+ * Sparse Z for many classes.  Section 3 keeps the embedding as a sparse matrix; with
+ * K >> 64 the dense [N][K] array would dominate the bytes.  Row i of Z holds one entry for
+ * every class that occurs among the labels of i's neighbours (an unlabelled neighbour
+ * counts in no class) and, with GEE_DIAG_AUG, for i's own class when i is labelled: the
+ * structure of the sparse product (A (+ I)) W.  The values are those of Eq. 1 with the
+ * Table 1 options, as in gee_embed (the 2-norm runs over the row's entries); an entry can
+ * be 0 (weights that cancel, a degree of 0 under GEE_LAPLACIAN).
+ *
+ *   K                1 .. GEE_MAX_K_SPARSE classes (labels in [-1, K))
+ *   d_zrowptr        device int32 [N+1] out: row i's entries are [zrowptr[i], zrowptr[i+1])
+ *   d_zcol, d_zval   device int32 / float32 [zcap] out: classes (ascending within a row) and
+ *                    values
+ *   zcap             room in d_zcol/d_zval, at least E + N (2E + N with GEE_SYMMETRIZE):
+ *                    the most entries Z can have (GEE_ERR_ARG otherwise)
+ *   d_workspace      gee_sparse_workspace_size bytes, 256-byte aligned
+ * A row's sums run in a fixed order for a given graph and options (the same bits on every
+ * call); the order differs from gee_embed's, so the values agree with it to rounding.
+ * Stream-ordered, no allocation; errors and status bits as gee_embed.  The tuning fields
+ * of opts apply to the CSR build (hub_threshold) only.
+ */
+#define GEE_MAX_K_SPARSE (1 << 20)
+size_t gee_sparse_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts);
+int gee_embed_sparse(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                     const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_zrowptr, int32_t *d_zcol,
+                     float *d_zval, int64_t zcap, void *d_workspace, size_t workspace_bytes, void *stream,
+                     uint32_t *d_status);
+
+/* ------------------------------------------------------------------------------------
  * One graph split by source rows over several GPUs (one process per GPU).  Rows are
  * independent once the node table {y_j, s_j = D_jj^-1/2 / n_{y_j}} of every node is known
  * (Section 2: Z_i^k sums e_ij W_j^k over the row's own entries), so a rank that owns rows

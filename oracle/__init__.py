@@ -12,6 +12,8 @@ Two independent forms of the same definitions:
 * ``embed_rows`` is the same edge-list oracle restated row by row on several host threads
   (``gee_oracle_rows.c``): it is the all-core CPU baseline, bit-identical to ``embed``
   because each row's sums keep the edge-list order.
+* ``embed_sparse`` keeps Z sparse (Section 3): per row the classes of its labelled
+  neighbours (+ its own with augmentation), each value equal to ``embed``'s bit for bit.
 
 Parity pinning: every function here is checked in ``tests/test_oracle.py`` against
 closed forms, invariants, a library stable sort, brute force on tiny inputs and the
@@ -64,6 +66,8 @@ def _load():
         lib.oracle_symmetrize.restype = i64
         lib.oracle_embed_rows.argtypes = [P, P, P, i64, i32, P, i32, u32, ctypes.c_int, P]
         lib.oracle_embed_rows.restype = ctypes.c_int
+        lib.oracle_embed_sparse.argtypes = [P, P, P, i64, i32, P, i32, u32, P, P, P]
+        lib.oracle_embed_sparse.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -136,6 +140,26 @@ def embed(src, dst, w, N, labels, K, flags=0) -> np.ndarray:
     if err:
         raise ValueError(f"oracle: invalid input (error bits {err})")
     return Z
+
+
+def embed_sparse(src, dst, w, N, labels, K, flags=0):
+    """Sparse Z (Section 3): (zrowptr int64 [N+1], zcol int32, zval float64) with, per row,
+    the classes of its labelled neighbours (+ its own with augmentation) ascending."""
+    src, dst, w, y = _i32(src), _i32(dst), _f32(w), _i32(labels)
+    E = src.size
+    zrowptr = np.zeros(N + 1, np.int64)
+    zcol = np.zeros(E + N + 1, np.int32)
+    zval = np.zeros(E + N + 1, np.float64)
+    err = _load().oracle_embed_sparse(_ptr(src), _ptr(dst), _ptr(w), E, N, _ptr(y), K, flags, _ptr(zrowptr),
+                                      _ptr(zcol), _ptr(zval))
+    if err:
+        raise ValueError(f"invalid input (oracle error bits {err})")
+    n = int(zrowptr[N])
+    return zrowptr, zcol[:n], zval[:n]
+
+
+def embed_sparse_graph(g, flags=0):
+    return embed_sparse(g.src, g.dst, g.w, g.N, g.labels, g.K, flags)
 
 
 def embed_graph(g, flags=0) -> np.ndarray:

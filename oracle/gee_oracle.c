@@ -138,6 +138,100 @@ void oracle_class_counts(const int32_t *src, const int32_t *dst, int64_t E, int3
     }
 }
 
+/* Z kept sparse (Section 3): for each row i, the classes that occur among the labels of
+ * i's neighbours (and i's own class with augmentation, when i is labelled), ascending,
+ * with their values of Eq. 1 and the Table 1 options: the structure of the sparse
+ * product (A (+ I)) W.  Each row's terms are added in edge-list order, as in oracle_embed,
+ * into a per-row accumulator over the K classes, so every stored value equals
+ * oracle_embed's entry bit for bit.  zrowptr [N+1], zcol / zval with room for E + N
+ * entries.  Returns the validation error bits; the outputs are only written when 0. */
+int oracle_embed_sparse(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
+                        const int32_t *y, int32_t K, uint32_t flags, int64_t *zrowptr, int32_t *zcol,
+                        double *zval) {
+    int err = oracle_validate(src, dst, w, E, N, y, K, flags);
+    if (err) return err;
+    int64_t *nk = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    oracle_label_counts(y, N, K, nk);
+    double *dinv = NULL;
+    if (flags & ORACLE_LAPLACIAN) {
+        dinv = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+        oracle_degrees(src, w, E, N, flags, dinv);
+        for (int32_t i = 0; i < N; ++i) dinv[i] = dinv[i] > 0.0 ? 1.0 / sqrt(dinv[i]) : 0.0;
+    }
+    /* the edges of every row, in edge-list order */
+    int64_t *start = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(E > 0 ? E : 1));
+    for (int64_t e = 0; e < E; ++e) start[src[e] + 1] += 1;
+    for (int32_t i = 0; i < N; ++i) start[i + 1] += start[i];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int32_t i = 0; i < N; ++i) fill[i] = start[i];
+    for (int64_t e = 0; e < E; ++e) order[fill[src[e]]++] = e;
+    double *acc = (double *)calloc((size_t)K, sizeof(double));
+    char *seen = (char *)calloc((size_t)K, 1);
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    int64_t out = 0;
+    for (int32_t i = 0; i < N; ++i) {
+        int32_t nt = 0;
+        for (int64_t t = start[i]; t < start[i + 1]; ++t) {
+            const int64_t e = order[t];
+            const int32_t j = dst[e], k = y[j];
+            if (k < 0) continue;
+            double a = w ? (double)w[e] : 1.0;
+            if (dinv) a = dinv[i] * a * dinv[j];
+            acc[k] += a * weight_matrix_entry(y, nk, j, k);
+            if (!seen[k]) {
+                seen[k] = 1;
+                touched[nt++] = k;
+            }
+        }
+        if ((flags & ORACLE_DIAG_AUG) && y[i] >= 0) {
+            const int32_t k = y[i];
+            double a = 1.0;
+            if (dinv) a = dinv[i] * a * dinv[i];
+            acc[k] += a * weight_matrix_entry(y, nk, i, k);
+            if (!seen[k]) {
+                seen[k] = 1;
+                touched[nt++] = k;
+            }
+        }
+        /* ascending classes (insertion sort: rows are short in the tests) */
+        for (int32_t u = 1; u < nt; ++u) {
+            const int32_t v = touched[u];
+            int32_t q = u - 1;
+            while (q >= 0 && touched[q] > v) {
+                touched[q + 1] = touched[q];
+                --q;
+            }
+            touched[q + 1] = v;
+        }
+        double r = 1.0;
+        if (flags & ORACLE_CORRELATION) {
+            double s2 = 0.0;
+            for (int32_t u = 0; u < nt; ++u) s2 += acc[touched[u]] * acc[touched[u]];
+            r = sqrt(s2);
+        }
+        zrowptr[i] = out;
+        for (int32_t u = 0; u < nt; ++u) {
+            const int32_t k = touched[u];
+            zcol[out] = k;
+            zval[out] = ((flags & ORACLE_CORRELATION) && r > 0.0) ? acc[k] / r : acc[k];
+            ++out;
+            acc[k] = 0.0;
+            seen[k] = 0;
+        }
+    }
+    zrowptr[N] = out;
+    free(touched);
+    free(seen);
+    free(acc);
+    free(fill);
+    free(order);
+    free(start);
+    free(dinv);
+    free(nk);
+    return 0;
+}
+
 /* The embedding Z (N x K, row-major, double), edge-list form of Eq. 1 with the options
  * of Table 1.  Returns the validation error bits; Z is only written when they are 0. */
 int oracle_embed(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,

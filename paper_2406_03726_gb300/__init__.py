@@ -28,6 +28,8 @@ from ._native import (  # noqa: F401
     make_graphs,
     gee_build_csr,
     gee_class_counts,
+    gee_embed_sparse,
+    gee_sparse_workspace_size,
     gee_embed,
     gee_embed_host,
     gee_embed_static,
@@ -77,6 +79,7 @@ PHASES = ("memset", "k_prep", "k_offsets_first", "k_scatter_first", "k_count", "
 MAX_N = 1 << 21
 MAX_E = 1 << 30
 MAX_K = 64
+MAX_K_SPARSE = 1 << 20
 
 
 class GeeError(RuntimeError):
@@ -154,6 +157,28 @@ def build_csr(src, dst, w, N, labels, K, flags=0, hub_threshold=0, lanes_per_row
         used = int(rowptr[N].item())
         col, val = col[:used], val[:used]
     return rowptr, col, val, nk, deg
+
+
+def embed_sparse(src, dst, w, N, labels, K, flags=0, status=None, stream=None, opts=None):
+    """Sparse Z (CSR over classes): (zrowptr int32 [N+1], zcol int32 [nnz], zval float32 [nnz]),
+    for any K up to MAX_K_SPARSE.  Row i lists the classes of its labelled neighbours (and
+    its own class with DIAG_AUG), ascending."""
+    import torch
+    E = int(src.numel()) if src is not None else 0
+    dev = labels.device
+    o = opts if opts is not None else make_opts(flags)
+    n = gee_sparse_workspace_size(E, N, K, w is not None, o)
+    if n == 0:
+        raise GeeError(1, "gee_sparse_workspace_size")
+    ws = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    cap = (2 * E if o.flags & SYMMETRIZE else E) + N
+    zrowptr = torch.empty(N + 1, dtype=torch.int32, device=dev)
+    zcol = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    zval = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+    rc = gee_embed_sparse(src, dst, w, E, N, labels, K, o, zrowptr, zcol, zval, cap, ws, ws.numel(), stream, status)
+    _check(rc, "gee_embed_sparse")
+    nnz = int(zrowptr[N].item())
+    return zrowptr, zcol[:nnz], zval[:nnz]
 
 
 def class_counts(rowptr, col, N, labels, K, stream=None):

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "gee_tune_cache_clear": ([], ctypes.c_int),
     "gee_reembed": ([_P, _I64, _I32, _I32, ctypes.c_int, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
     "gee_shard_workspace_size": ([_I64, _I32, _I32, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_sparse_workspace_size": ([_I64, _I32, _I32, ctypes.c_int, _P], _SZ),
+    "gee_embed_sparse": ([_P, _P, _P, _I64, _I32, _P, _I32, _P, _P, _P, _P, _I64, _P, _SZ, _P, _P], ctypes.c_int),
     "gee_shard_build": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _I32, _P, _P, _P, _SZ, _P, _P], ctypes.c_int),
     "gee_shard_table": ([_I64, _I32, _I32, _I32, _P, _I32, ctypes.c_int, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
     "gee_shard_embed": ([_I64, _I32, _I32, _I32, _P, _I32, ctypes.c_int, _P, _P, _P, _P, _SZ, _P, _P],
@@ -217,6 +219,17 @@ def gee_graph_cache_clear() -> int:
 def gee_reembed(labels, E, N, K, weighted, opts, Z, workspace, workspace_bytes, stream=None, d_status=None) -> int:
     return lib().gee_reembed(ptr(labels), E, N, K, int(bool(weighted)), _opts_ref(opts), ptr(Z), ptr(workspace),
                              workspace_bytes, stream_handle(stream), ptr(d_status))
+
+
+def gee_sparse_workspace_size(E, N, K, weighted, opts=None) -> int:
+    return lib().gee_sparse_workspace_size(E, N, K, int(bool(weighted)), _opts_ref(opts))
+
+
+def gee_embed_sparse(src, dst, w, E, N, labels, K, opts, zrowptr, zcol, zval, zcap, workspace, workspace_bytes,
+                     stream=None, d_status=None) -> int:
+    return lib().gee_embed_sparse(ptr(src), ptr(dst), ptr(w), E, N, ptr(labels), K, _opts_ref(opts), ptr(zrowptr),
+                                  ptr(zcol), ptr(zval), zcap, ptr(workspace), workspace_bytes, stream_handle(stream),
+                                  ptr(d_status))
 
 
 def gee_shard_workspace_size(E, N, r0, r1, K, weighted, opts=None) -> int:

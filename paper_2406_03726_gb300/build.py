@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libgee.so")
-SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu", "csrc/gee_static.cu", "csrc/gee_server.cu"]
-HEADERS = ["csrc/gee_internal.cuh"]
+SOURCES = ["csrc/gee_kernels.cu", "csrc/gee_api.cu", "csrc/gee_static.cu", "csrc/gee_server.cu",
+           "csrc/gee_sparse.cu"]
+HEADERS = ["csrc/gee_internal.cuh", "csrc/gee_sparse.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "-Xcompiler", "-pthread",

@@ -7,6 +7,7 @@
 // and k_spmm.  Nothing is
 // allocated and nothing synchronises, so the sequence can be captured in a CUDA graph.
 #include "gee_internal.cuh"
+#include "gee_sparse.cuh"
 #include "../../include/gee.h"
 
 #include <cuda_runtime.h>
@@ -65,7 +66,7 @@ int device_info(DeviceInfo &out) {
     DeviceInfo &d = g_dev[dev];
     if (!d.ready) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEE_ERR_CUDA;
-        if (configure_kernels() != cudaSuccess) return GEE_ERR_CUDA;
+        if (configure_kernels() != cudaSuccess || configure_sparse_kernels() != cudaSuccess) return GEE_ERR_CUDA;
         for (int v = 0; v < 3; ++v)
             for (int i = 0; i < 8; ++i)
                 for (int w = 0; w < 2; ++w) d.occ_spmm[v][i][w] = occupancy_spmm(8 * (i + 1), 2 << v, w != 0);
@@ -471,8 +472,10 @@ struct SinglePlan {
 };
 
 // cols / row0: column range and first row of a row shard (cols < 0: a whole graph)
+// kmax < 0: the product kernel's classes are K (the sparse path, which does not run it,
+// passes 1)
 void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, SinglePlan &p, int32_t cols = -1,
-                 int32_t row0 = 0) {
+                 int32_t row0 = 0, int32_t kmax = -1) {
     std::memset(&p.d, 0, sizeof(p.d));
     std::memset(&p.cb, 0, sizeof(p.cb));
     plan_params(s, o, want_deg, p.d);
@@ -483,7 +486,7 @@ void plan_single(const Shape &s, const gee_opts &o, bool want_deg, char *base, S
     }
     p.cb.hub_cap = hub_cap_of(p.d);
     p.cb.chunk_cap = chunk_cap_of(p.d);
-    p.cb.kmax = s.K;
+    p.cb.kmax = kmax >= 0 ? kmax : s.K;
     Bump b{base};
     layout_call_zero(b, p.cb);
     p.d.status = b.take<uint32_t>(1);
@@ -1374,6 +1377,107 @@ int gee_embed_host(const int32_t *src, const int32_t *dst, const float *w, int64
     GEE_TRY(cuda_check(cudaStreamSynchronize(st)));
     if (status) *status = h_status;
     return h_status ? GEE_ERR_DATA : GEE_OK;
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// Sparse Z (CSR over classes) for many classes
+
+namespace gee {
+namespace {
+
+int check_sparse_shape(int64_t E, int32_t N, int32_t K) {
+    if (E < 0 || N < 0 || K < 1) return GEE_ERR_ARG;
+    if (N > GEE_MAX_N || E >= GEE_MAX_E || K > GEE_MAX_K_SPARSE) return GEE_ERR_TOO_LARGE;
+    return GEE_OK;
+}
+
+// The CSR build's plan (no product-kernel buffers), then the sparse path's scratch.
+void plan_sparse(const Shape &s, const gee_opts &o, char *base, SinglePlan &p, SparseArgs &a, size_t &total) {
+    plan_single(s, o, false, base, p, -1, 0, 1);
+    Bump b{base};
+    b.off = p.total_bytes;
+    const int64_t E = p.d.E, N = s.N;
+    std::memset(&a, 0, sizeof(a));
+    a.cnt = b.take<int32_t>((size_t)N);
+    a.long_cap = (uint32_t)sparse_long_cap(E);
+    a.long_list = b.take<int32_t>(a.long_cap);
+    a.long_count = b.take<uint32_t>(1);
+    a.tile_sum = b.take<uint32_t>((size_t)sparse_scan_tiles(s.N) + 1);
+    a.runs_a = b.take<int4>((size_t)(E + N));
+    a.runs_b = b.take<int4>((size_t)(E + N));
+    total = (b.off + kAlign - 1) & ~(kAlign - 1);
+}
+
+}  // namespace
+}  // namespace gee
+
+extern "C" {
+
+size_t gee_sparse_workspace_size(int64_t E, int32_t N, int32_t K, int weighted, const gee_opts *opts) {
+    if (check_sparse_shape(E, N, K) != GEE_OK) return 0;
+    const gee_opts o = opts_or_default(opts);
+    if (check_opts(o) != GEE_OK) return 0;
+    SinglePlan p;
+    SparseArgs a;
+    size_t total = 0;
+    plan_sparse(Shape{E, N, K, weighted != 0}, o, nullptr, p, a, total);
+    return total;
+}
+
+int gee_embed_sparse(const int32_t *d_src, const int32_t *d_dst, const float *d_w, int64_t E, int32_t N,
+                     const int32_t *d_labels, int32_t K, const gee_opts *opts, int32_t *d_zrowptr, int32_t *d_zcol,
+                     float *d_zval, int64_t zcap, void *d_workspace, size_t workspace_bytes, void *stream,
+                     uint32_t *d_status) {
+    GEE_TRY(check_sparse_shape(E, N, K));
+    GEE_TRY(check_inputs(d_src, d_dst, E, N, d_labels));
+    const gee_opts o = opts_or_default(opts);
+    GEE_TRY(check_opts(o));
+    const int64_t entries = (o.flags & GEE_SYMMETRIZE) ? 2 * E : E;
+    if (!d_zrowptr || (N > 0 && (!d_zcol || !d_zval)) || zcap < entries + N) return GEE_ERR_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        GEE_TRY(cuda_check(cudaMemsetAsync(d_zrowptr, 0, sizeof(int32_t), st)));
+        if (d_status) GEE_TRY(cuda_check(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st)));
+        return GEE_OK;
+    }
+    DeviceInfo dev;
+    GEE_TRY(device_info(dev));
+    const Shape s{E, N, K, d_w != nullptr};
+    SinglePlan p;
+    SparseArgs a;
+    size_t total = 0;
+    plan_sparse(s, o, nullptr, p, a, total);
+    GEE_TRY(check_ws(d_workspace, workspace_bytes, total));
+    plan_sparse(s, o, static_cast<char *>(d_workspace), p, a, total);
+    p.d.src = d_src;
+    p.d.dst = d_dst;
+    p.d.w = d_w;
+    p.d.y = d_labels;
+    p.d.Z = nullptr;
+    GEE_TRY(run_single(p, dev, st, nullptr, false));  // CSR, degrees, node table
+    const GraphDesc &d = p.d;
+    a.rowptr = d.rowptr;
+    a.col = d.col;
+    a.val = d.val;
+    a.y = d_labels;
+    a.tab = d.tab;
+    a.dinv = d.dinv;
+    a.N = N;
+    a.K = K;
+    a.E = d.E;
+    a.flags = o.flags & (GEE_DIAG_AUG | GEE_LAPLACIAN | GEE_CORRELATION);
+    a.zrowptr = d_zrowptr;
+    a.zcol = d_zcol;
+    a.zval = d_zval;
+    a.zcap = zcap;
+    a.status = d.status;
+    GEE_TRY(cuda_check(cudaMemsetAsync(a.long_count, 0, sizeof(uint32_t), st)));
+    GEE_TRY(cuda_check(launch_sparse(a, dev.sms, st)));
+    if (d_status)
+        GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));
+    return GEE_OK;
 }
 
 }  // extern "C"

@@ -370,16 +370,21 @@ __global__ void __launch_bounds__(kThreads) k_prep(const __grid_constant__ Ctx c
         const int64_t n0 = (int64_t)(t - sg.ranges) * kPrepTile;
         const int n = (int)min64(kPrepTile, (int64_t)sg.N - n0);
         const int K = sg.K;
-        for (int i = tid; i < K; i += kThreads) h[i] = 0;
+        // class sizes in shared memory, or straight into n_k when the classes outnumber
+        // the histogram (sparse Z with many classes)
+        const bool local = K <= kWarps * kPrivDigits;
+        if (local)
+            for (int i = tid; i < K; i += kThreads) h[i] = 0;
         __syncthreads();
         for (int i = tid; i < n; i += kThreads) {
             int yv = __ldg(sg.y + n0 + i);
             if (yv < -1 || yv >= K) err |= kStLabel;
-            else if (yv >= 0) atomicAdd(&h[yv], 1u);
+            else if (yv >= 0) atomicAdd(local ? &h[yv] : reinterpret_cast<unsigned *>(sg.nk) + yv, 1u);
         }
         __syncthreads();
-        for (int i = tid; i < K; i += kThreads)
-            if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h[i]);
+        if (local)
+            for (int i = tid; i < K; i += kThreads)
+                if (h[i]) atomicAdd(reinterpret_cast<unsigned *>(sg.nk) + i, h[i]);
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();

@@ -25,6 +25,9 @@ int oracle_embed(const int32_t *src, const int32_t *dst, const float *w, int64_t
                  const int32_t *y, int32_t K, uint32_t flags, double *Z);
 int oracle_embed_rows(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
                       const int32_t *y, int32_t K, uint32_t flags, int threads, double *Z);
+int oracle_embed_sparse(const int32_t *src, const int32_t *dst, const float *w, int64_t E, int32_t N,
+                        const int32_t *y, int32_t K, uint32_t flags, int64_t *zrowptr, int32_t *zcol,
+                        double *zval);
 
 static uint64_t rng_state;
 
@@ -93,6 +96,23 @@ static void run_case(int32_t N, int64_t E, int32_t K, int weighted) {
                   "row-parallel form is bit-identical", N, E, flags);
         }
         for (int64_t q = 0; q < (int64_t)N * K; ++q) check(isfinite(Z[q]), "finite Z", N, E, flags);
+        {  /* the sparse form: every stored value is the dense entry, bit for bit */
+            int64_t *zr = malloc(sizeof(int64_t) * (size_t)(N + 1));
+            int32_t *zc = malloc(sizeof(int32_t) * (size_t)(E + N + 1));
+            double *zv = malloc(sizeof(double) * (size_t)(E + N + 1));
+            check(oracle_embed_sparse(src, dst, w, E, N, y, K, flags, zr, zc, zv) == 0, "sparse form runs", N, E,
+                  flags);
+            check(zr[0] == 0 && zr[N] <= E + N, "sparse index pointers", N, E, flags);
+            for (int32_t i = 0; i < N; ++i)
+                for (int64_t t = zr[i]; t < zr[i + 1]; ++t) {
+                    check(zc[t] >= 0 && zc[t] < K && (t == zr[i] || zc[t - 1] < zc[t]), "sparse classes ascend", N, E,
+                          flags);
+                    check(zv[t] == Z[(int64_t)i * K + zc[t]], "sparse value is the dense entry", N, E, flags);
+                }
+            free(zv);
+            free(zc);
+            free(zr);
+        }
         if (flags == 0 && !w)  /* Z n_k equals the class counts (Eq. 1 with one-hot W / n_k) */
             for (int64_t q = 0; q < (int64_t)N * K; ++q) {
                 const double c = (double)C[q];

@@ -136,6 +136,7 @@ def test_python_constants_match_header(tmp_path):
              "GEE_STATUS_INTERNAL": gee.STATUS_INTERNAL, "GEE_STATUS_STALE": gee.STATUS_STALE,
              "GEE_ERR_NOMEM": gee.ERR_NOMEM, "GEE_PENDING": gee.PENDING, "GEE_ERR_STATE": gee.ERR_STATE,
              "GEE_MAX_N": gee.MAX_N, "GEE_MAX_E": gee.MAX_E, "GEE_MAX_K": gee.MAX_K,
+             "GEE_MAX_K_SPARSE": gee.MAX_K_SPARSE,
              "GEE_NUM_PHASES": len(gee.PHASES)}
     body = "".join(f'printf("{k} %lld\\n", (long long)({k}));\n' for k in pairs)
     got = dict((k, int(v)) for k, v in (line.split() for line in _c_layout(tmp_path, body).splitlines()))

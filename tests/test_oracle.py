@@ -345,3 +345,56 @@ def test_symmetrized_one_direction_reproduces_the_undirected_graph():
         Z = oracle.embed_graph(g, f)
         Zs = oracle.embed(s, d, w, g.N, g.labels, g.K, f)
         assert np.allclose(Zs, Z, rtol=1e-12, atol=1e-15), f
+
+
+def _sparse_structure(g, flags):
+    """Brute force: the classes of each row's labelled neighbours, plus its own class with
+    augmentation when it is labelled."""
+    rows = [set() for _ in range(g.N)]
+    for s, d in zip(g.src, g.dst):
+        if g.labels[d] >= 0:
+            rows[s].add(int(g.labels[d]))
+    if flags & 1:
+        for i in range(g.N):
+            if g.labels[i] >= 0:
+                rows[i].add(int(g.labels[i]))
+    return [sorted(r) for r in rows]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sparse_z_is_the_dense_z_on_its_structure(seed):
+    # Section 3 keeps Z sparse: the structure is that of (A (+I)) W, the values the dense
+    # oracle's, bit for bit; every entry outside the structure is an exact zero
+    g = random_tiny(seed, n_max=80, e_max=600, weighted=(seed % 2 == 0))
+    for flags in ALL_FLAGS:
+        rp, zc, zv = oracle.embed_sparse_graph(g, flags)
+        Z = oracle.embed_graph(g, flags)
+        struct = _sparse_structure(g, flags)
+        assert rp[0] == 0 and np.all(np.diff(rp) >= 0)
+        dense_from_sparse = np.zeros_like(Z)
+        for i in range(g.N):
+            cols = zc[rp[i]:rp[i + 1]]
+            assert list(cols) == struct[i], (seed, flags, i)
+            dense_from_sparse[i, cols] = zv[rp[i]:rp[i + 1]]
+        assert np.array_equal(dense_from_sparse, Z), (seed, flags)
+
+
+def test_sparse_z_with_many_classes():
+    # K far above the dense limit: a star whose leaves carry distinct classes, plus a ring
+    N, K = 3001, 50000
+    hub = 0
+    src = np.concatenate([np.zeros(N - 1, np.int32), np.arange(1, N, dtype=np.int32)])
+    dst = np.concatenate([np.arange(1, N, dtype=np.int32), np.zeros(N - 1, np.int32)])
+    y = (np.arange(N, dtype=np.int32) * 7) % K
+    rp, zc, zv = oracle.embed_sparse(src, dst, None, N, y, K, 0)
+    # the hub's row: one entry per leaf class, each 1 / n_k = 1 (every class holds one node)
+    hub_cols = zc[rp[hub]:rp[hub + 1]]
+    assert np.array_equal(hub_cols, np.sort(y[1:]))
+    assert np.all(zv[rp[hub]:rp[hub + 1]] == 1.0)
+    # a leaf's row: the hub's class only
+    assert rp[2] - rp[1] == 1 and zc[rp[1]] == y[hub]
+    # with augmentation and correlation every row is unit-norm
+    rp, zc, zv = oracle.embed_sparse(src, dst, None, N, y, K, 5)
+    for i in (0, 1, 1500):
+        v = zv[rp[i]:rp[i + 1]]
+        assert abs(np.sqrt(np.sum(v * v)) - 1.0) < 1e-12
