@@ -1404,7 +1404,11 @@ void plan_sparse(const Shape &s, const gee_opts &o, char *base, SinglePlan &p, S
     a.long_cap = (uint32_t)sparse_long_cap(E);
     a.long_list = b.take<int32_t>(a.long_cap);
     a.long_count = b.take<uint32_t>(1);
+    a.chunk_cap = (uint32_t)sparse_chunk_cap(E);
+    a.chunk_off = b.take<uint32_t>((size_t)a.long_cap + 1);
+    a.chunk_cnt = b.take<int32_t>(a.chunk_cap);
     a.tile_sum = b.take<uint32_t>((size_t)sparse_scan_tiles(s.N) + 1);
+    a.wstart = b.take<int32_t>((size_t)sparse_windows(E) + 1);
     a.runs_a = b.take<int4>((size_t)(E + N));
     a.runs_b = b.take<int4>((size_t)(E + N));
     total = (b.off + kAlign - 1) & ~(kAlign - 1);

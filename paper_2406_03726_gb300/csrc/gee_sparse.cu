@@ -30,7 +30,7 @@ namespace gee {
 namespace {
 
 constexpr int kZsWin = 1024;                  // window of CSR positions per k_zs_rows CTA
-constexpr int kZsTile = 4096;                 // entries a window can hold (<= 3 kZsWin - 1)
+constexpr int kZsTile = 3 * kZsWin;           // entries a window can hold (at most 3 kZsWin - 1)
 constexpr int kZsChunk = 2048;                // entries per chunk of a long row
 constexpr int kZsScanTile = 2048;             // rows per tile of the count scan
 constexpr uint32_t kZsNoClass = 0x1fffffu;    // class field of an unlabelled neighbour
@@ -111,6 +111,42 @@ __device__ void zs_sort(uint64_t *key, float *val, int n) {
         }
 }
 
+// Sort key[0..L) ascending (with their values) by one warp, in place: the bitonic network
+// in its all-ascending form (each merge first compares i with its mirror in the block,
+// then half-cleaners), so every compare-exchange puts the smaller key at the lower index
+// and positions at or past L, which act as +infinity, are never touched.
+__device__ void zs_warp_sort(uint64_t *key, float *val, int L, int lane) {
+    int P = 1;
+    while (P < L) P <<= 1;
+    auto ce = [&](int i, int j) {
+        if (j < L) {
+            const uint64_t a = key[i], b = key[j];
+            if (a > b) {
+                key[i] = b;
+                key[j] = a;
+                const float t = val[i];
+                val[i] = val[j];
+                val[j] = t;
+            }
+        }
+    };
+    for (int k = 2; k <= P; k <<= 1) {
+        const int h = k >> 1;
+        for (int t = lane; t < (P >> 1); t += 32) {
+            const int b = t / h, o = t - b * h;
+            ce(b * k + o, b * k + k - 1 - o);
+        }
+        __syncwarp();
+        for (int d = k >> 2; d > 0; d >>= 1) {
+            for (int t = lane; t < (P >> 1); t += 32) {
+                const int i = (t / d) * 2 * d + (t % d);
+                ce(i, i + d);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // Inclusive segmented sum of val[0..n) over runs of equal (key >> shift), in place
 // (Hillis-Steele with segment flags: a fixed tree for a given run position, so the result
 // is reproducible).  v2/f/f2 are scratch of n entries.
@@ -145,12 +181,25 @@ __device__ void zs_segsum(const uint64_t *key, float *val, float *v2, uint8_t *f
 
 __device__ __forceinline__ float node_s(const SparseArgs &a, int j) { return __int_as_float(__ldg(&a.tab[j]).y); }
 
+// First row of every window: wstart[w] = the first row with rowptr >= w * kZsWin, for the
+// windows 0 .. E / kZsWin + 1 (the last entry is N).
+__global__ void __launch_bounds__(kThreads) k_zs_wstart(const __grid_constant__ SparseArgs a, int windows) {
+    for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r <= a.N; r += (int64_t)gridDim.x * kThreads) {
+        // the windows (w_prev, w_r] start at row r; row N stands for the end
+        const int64_t wr = r < a.N ? (int64_t)__ldg(a.rowptr + r) / kZsWin : (int64_t)windows;
+        const int64_t wp = r > 0 ? (int64_t)__ldg(a.rowptr + r - 1) / kZsWin : -1;
+        for (int64_t w = wp + 1; w <= wr && w <= windows; ++w) a.wstart[w] = (int32_t)r;
+    }
+}
+
 // ---- k_zs_rows ----------------------------------------------------------------------------
 struct ZsRowsSmem {
     uint64_t key[kZsTile];
     float val[kZsTile];
-    float v2[kZsTile];
-    uint32_t t[kZsTile + 1];      // tail flags, then their exclusive scan
+    union {                       // the segmented sum's scratch, then the tail flags and
+        float v2[kZsTile + 1];    // their exclusive scan
+        uint32_t t[kZsTile + 1];
+    };
     uint8_t f[kZsTile], f2[kZsTile];
     int32_t rowid[kZsWin];        // rows of the window with 1..kZsWin entries, in order
     uint32_t roff[kZsWin + 1];    // their first tile position
@@ -164,18 +213,8 @@ __global__ void __launch_bounds__(kThreads) k_zs_rows(const __grid_constant__ Sp
     ZsRowsSmem &S = *reinterpret_cast<ZsRowsSmem *>(zs_smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool aug = (a.flags & kOptAug) != 0;
-    const int64_t w0 = (int64_t)blockIdx.x * kZsWin, w1 = w0 + kZsWin;
     uint32_t err = 0;
-    if (tid < 2) {  // rows [ra, rb): the first rows with rowptr >= w0 and >= w1
-        const int64_t target = tid == 0 ? w0 : w1;
-        int lo = 0, hi = a.N;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((int64_t)__ldg(a.rowptr + mid) < target) lo = mid + 1;
-            else hi = mid;
-        }
-        S.s_range[tid] = lo;
-    }
+    if (tid < 2) S.s_range[tid] = __ldcg(a.wstart + blockIdx.x + tid);  // rows [ra, rb) start in the window
     if (tid == 0) {
         S.s_nm = 0;
         S.s_ne = 0;
@@ -231,37 +270,66 @@ __global__ void __launch_bounds__(kThreads) k_zs_rows(const __grid_constant__ Sp
     if (tid == 0) S.roff[nm] = (uint32_t)ne;
     __syncthreads();
     if (nm > 0) {
-        int n2 = 32;
-        while (n2 < ne) n2 <<= 1;
-        for (int i = ne + tid; i < n2; i += kThreads) {
-            S.key[i] = kZsPad;
-            S.val[i] = 0.0f;
-        }
-        // ---- load: one warp per row, lanes over its entries (and its augmentation term)
-        for (int mi = warp; mi < nm; mi += kWarps) {
-            const int r = S.rowid[mi];
-            const int64_t p0 = __ldg(a.rowptr + r);
-            const int o = (int)S.roff[mi];
-            const int tot = (int)S.roff[mi + 1] - o;
-            const int len = (int)(__ldg(a.rowptr + r + 1) - p0);
-            for (int e = lane; e < tot; e += 32) {
+        const int n2 = ne;
+        // ---- load the window's entries with every thread, 8 at a time, so that the column,
+        // label and node-table reads of many entries are in flight together; entry p of
+        // the tile belongs to the last short row with roff <= p
+        constexpr int kBatch = 8;
+        for (int p0b = 0; p0b < ne; p0b += kThreads * kBatch) {
+            int mi[kBatch], e[kBatch], j[kBatch];
+            int64_t q[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int p = p0b + u * kThreads + tid;
+                mi[u] = -1;
+                e[u] = 0;
+                j[u] = 0;
+                q[u] = 0;
+                if (p < ne) {
+                    int lo = 0, hi = nm;  // last row with roff <= p
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if ((int)S.roff[mid] <= p) lo = mid;
+                        else hi = mid;
+                    }
+                    mi[u] = lo;
+                    e[u] = p - (int)S.roff[lo];
+                    q[u] = (int64_t)__ldg(a.rowptr + S.rowid[lo]) + e[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (mi[u] < 0) continue;
+                const int r = S.rowid[mi[u]];
+                const int len = (int)(__ldg(a.rowptr + r + 1) - (q[u] - e[u]));
+                j[u] = e[u] < len ? min(max(__ldg(a.col + q[u]), 0), a.N - 1) : -1 - r;  // -1 - r: the augmentation term
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (mi[u] < 0) continue;
+                const int p = p0b + u * kThreads + tid;
                 uint32_t cls;
                 float v;
-                if (e < len) {
-                    const int j = min(max(__ldg(a.col + p0 + e), 0), a.N - 1);
-                    const int yj = __ldg(a.y + j);
+                if (j[u] >= 0) {
+                    const int yj = __ldg(a.y + j[u]);
                     cls = (yj >= 0 && yj < a.K) ? (uint32_t)yj : kZsNoClass;
-                    v = (a.val ? __ldg(a.val + p0 + e) : 1.0f) * node_s(a, j);
-                } else {  // the augmentation term, after the row's entries
+                    v = (a.val ? __ldg(a.val + q[u]) : 1.0f) * node_s(a, j[u]);
+                } else {
+                    const int r = -1 - j[u];
                     cls = (uint32_t)__ldg(a.y + r);
                     v = node_s(a, r);
                 }
-                S.key[o + e] = ((uint64_t)mi << 33) | ((uint64_t)cls << 12) | (uint64_t)e;
-                S.val[o + e] = v;
+                S.key[p] = ((uint64_t)mi[u] << 33) | ((uint64_t)cls << 12) | (uint64_t)e[u];
+                S.val[p] = v;
             }
         }
         __syncthreads();
-        zs_sort(S.key, S.val, n2);
+        // ---- each row's entries by (class, position): one warp per row
+        for (int m = warp; m < nm; m += kWarps) {
+            const int o = (int)S.roff[m];
+            zs_warp_sort(S.key + o, S.val + o, (int)S.roff[m + 1] - o, lane);
+        }
+        __syncthreads();
         zs_segsum(S.key, S.val, S.v2, S.f, S.f2, n2, 12);
         // ---- runs: the last entry of each (row, class) run holds its sum
         for (int i = tid; i < n2; i += kThreads) {
@@ -294,18 +362,118 @@ __global__ void __launch_bounds__(kThreads) k_zs_rows(const __grid_constant__ Sp
     if (err) atomicOr(a.status, err);
 }
 
-// ---- k_zs_long ----------------------------------------------------------------------------
+// ---- long rows: chunks sorted in parallel, then merged row by row -----------------------
+// A listed row of T = len (+1 augmentation term) entries has ceil(T / kZsChunk) chunks.
+// k_zs_long_plan numbers the chunks of all listed rows; k_zs_long_sort sorts and sums each
+// chunk (any CTA) into its sorted run list, stored in the row's slice of runs_b at
+// c * kZsChunk; k_zs_long_merge merges a row's chunk lists in chunk order (one CTA per row).
+
+__device__ __forceinline__ int long_row_entries(const SparseArgs &a, int r, int64_t &p0) {
+    p0 = __ldg(a.rowptr + r);
+    const int len = (int)(__ldg(a.rowptr + r + 1) - p0);
+    const int yi = __ldg(a.y + r);
+    return len + (((a.flags & kOptAug) && yi >= 0 && yi < a.K) ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_zs_long_plan(const __grid_constant__ SparseArgs a) {
+    __shared__ uint32_t s_warp[kWarps];
+    const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
+    uint32_t run = 0;
+    for (uint32_t b = 0; b < n; b += kThreads) {
+        const uint32_t li = b + threadIdx.x;
+        uint32_t m = 0;
+        if (li < n) {
+            const int r = min(max(__ldcg(a.long_list + li), 0), a.N - 1);
+            int64_t p0;
+            m = (uint32_t)((long_row_entries(a, r, p0) + kZsChunk - 1) / kZsChunk);
+        }
+        uint32_t tot;
+        const uint32_t x = zs_block_scan(m, s_warp, tot);
+        if (li < n) a.chunk_off[li] = run + x;
+        run += tot;
+    }
+    if (threadIdx.x == 0) a.chunk_off[n] = min(run, a.chunk_cap);
+    if (threadIdx.x == 0 && run > a.chunk_cap) atomicOr(a.status, kStInternal);
+}
+
 struct ZsLongSmem {
     uint64_t key[kZsChunk];
     float val[kZsChunk];
     float v2[kZsChunk];
-    uint32_t t[kZsChunk + 1];     // tail flags / scan, then unmatched flags / scan
+    uint32_t t[kZsChunk + 1];     // tail flags and their scan; unmatched flags and their scan
     uint8_t f[kZsChunk], f2[kZsChunk];
-    int32_t pc[kZsChunk];         // the chunk's runs: class, sum
+    int32_t pc[kZsChunk];         // a chunk's runs: class, sum
     float ps[kZsChunk];
     int32_t lba[kZsChunk];        // for each run: the runs of the list with a smaller class
     uint32_t s_warp[kWarps];
+    int32_t s_li;
 };
+
+__global__ void __launch_bounds__(kThreads) k_zs_long_sort(const __grid_constant__ SparseArgs a) {
+    extern __shared__ __align__(16) unsigned char zs_smem[];
+    ZsLongSmem &S = *reinterpret_cast<ZsLongSmem *>(zs_smem);
+    const int tid = threadIdx.x;
+    const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
+    const uint32_t chunks = n ? __ldcg(a.chunk_off + n) : 0u;
+    for (uint32_t gc = blockIdx.x; gc < chunks; gc += gridDim.x) {
+        if (tid == 0) {  // the listed row of this chunk: last li with chunk_off[li] <= gc
+            int lo = 0, hi = (int)n;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldcg(a.chunk_off + mid) <= gc) lo = mid;
+                else hi = mid;
+            }
+            S.s_li = lo;
+        }
+        __syncthreads();
+        const int li = S.s_li;
+        const int r = min(max(__ldcg(a.long_list + li), 0), a.N - 1);
+        int64_t p0;
+        const int T = long_row_entries(a, r, p0);
+        const int len = (int)(__ldg(a.rowptr + r + 1) - p0);
+        const int c0 = (int)(gc - __ldcg(a.chunk_off + li)) * kZsChunk;
+        const int nc = max(0, min(kZsChunk, T - c0));
+        int n2 = 32;
+        while (n2 < nc) n2 <<= 1;
+        for (int i = tid; i < n2; i += kThreads) {
+            uint64_t k = kZsPad;
+            float v = 0.0f;
+            if (i < nc) {
+                const int e = c0 + i;
+                if (e < len) {
+                    const int j = min(max(__ldg(a.col + p0 + e), 0), a.N - 1);
+                    const int yj = __ldg(a.y + j);
+                    if (yj >= 0 && yj < a.K) {
+                        k = ((uint64_t)yj << 32) | (uint64_t)e;
+                        v = (a.val ? __ldg(a.val + p0 + e) : 1.0f) * node_s(a, j);
+                    }
+                } else {
+                    k = ((uint64_t)__ldg(a.y + r) << 32) | (uint64_t)e;
+                    v = node_s(a, r);
+                }
+            }
+            S.key[i] = k;
+            S.val[i] = v;
+        }
+        __syncthreads();
+        zs_sort(S.key, S.val, n2);
+        zs_segsum(S.key, S.val, S.v2, S.f, S.f2, n2, 32);
+        for (int i = tid; i < n2; i += kThreads) {
+            const uint64_t k = S.key[i];
+            S.t[i] = (k != kZsPad && (i == n2 - 1 || (S.key[i + 1] >> 32) != (k >> 32))) ? 1u : 0u;
+        }
+        __syncthreads();
+        zs_scan_array(S.t, n2, S.s_warp);
+        int4 *out = a.runs_b + p0 + r + c0;  // the chunk's own part of the row's slice
+        for (int i = tid; i < n2; i += kThreads) {
+            const uint64_t k = S.key[i];
+            if (k != kZsPad && (i == n2 - 1 || (S.key[i + 1] >> 32) != (k >> 32)))
+                out[S.t[i]] = make_int4((int)(k >> 32), __float_as_int(S.val[i]), 0, 0);
+        }
+        if (tid == 0) a.chunk_cnt[gc] = (int32_t)S.t[n2];
+        __syncthreads();
+    }
+}
 
 __device__ __forceinline__ int lower_bound_runs(const int4 *A, int n, int c) {
     int lo = 0, hi = n;
@@ -317,66 +485,38 @@ __device__ __forceinline__ int lower_bound_runs(const int4 *A, int n, int c) {
     return lo;
 }
 
-__global__ void __launch_bounds__(kThreads) k_zs_long(const __grid_constant__ SparseArgs a) {
+__global__ void __launch_bounds__(kThreads) k_zs_long_merge(const __grid_constant__ SparseArgs a) {
     extern __shared__ __align__(16) unsigned char zs_smem[];
     ZsLongSmem &S = *reinterpret_cast<ZsLongSmem *>(zs_smem);
     const int tid = threadIdx.x;
-    const bool aug = (a.flags & kOptAug) != 0;
-    const uint32_t nlong = min(__ldcg(a.long_count), a.long_cap);
-    uint32_t err = 0;
-    for (uint32_t li = blockIdx.x; li < nlong; li += gridDim.x) {
+    const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
+    for (uint32_t li = blockIdx.x; li < n; li += gridDim.x) {
         const int r = min(max(__ldcg(a.long_list + li), 0), a.N - 1);
-        const int64_t p0 = __ldg(a.rowptr + r);
-        const int len = (int)(__ldg(a.rowptr + r + 1) - p0);
-        const int yi = __ldg(a.y + r);
-        const bool own = aug && yi >= 0 && yi < a.K;
-        const int T = len + (own ? 1 : 0);
-        int4 *cur = a.runs_a + p0 + r, *nxt = a.runs_b + p0 + r;
+        int64_t p0;
+        const int T = long_row_entries(a, r, p0);
+        const uint32_t g0 = __ldcg(a.chunk_off + li), g1 = __ldcg(a.chunk_off + li + 1);
+        int4 *const ra = a.runs_a + p0 + r, *const rb = a.runs_b + p0 + r;
         int na = 0;
-        for (int c0 = 0; c0 < T; c0 += kZsChunk) {
-            const int nc = min(kZsChunk, T - c0);
-            int n2 = 32;
-            while (n2 < nc) n2 <<= 1;
-            for (int i = tid; i < n2; i += kThreads) {
-                uint64_t k = kZsPad;
-                float v = 0.0f;
-                if (i < nc) {
-                    const int e = c0 + i;
-                    if (e < len) {
-                        const int j = min(max(__ldg(a.col + p0 + e), 0), a.N - 1);
-                        const int yj = __ldg(a.y + j);
-                        if (yj >= 0 && yj < a.K) {
-                            k = ((uint64_t)yj << 32) | (uint64_t)e;
-                            v = (a.val ? __ldg(a.val + p0 + e) : 1.0f) * node_s(a, j);
-                        }
-                    } else {
-                        k = ((uint64_t)yi << 32) | (uint64_t)e;
-                        v = node_s(a, r);
-                    }
-                }
-                S.key[i] = k;
-                S.val[i] = v;
+        // chunk numbers beyond the capacity (reported by the plan) or more chunks than
+        // the row's entries give: skip the row
+        const bool ok = g0 <= g1 && g1 <= a.chunk_cap &&
+                        (int64_t)(g1 - g0) <= ((int64_t)T + kZsChunk - 1) / kZsChunk;
+        const int m = ok ? (int)(g1 - g0) : 0;
+        for (int c = 0; c < m; ++c) {
+            // the chunk's runs into shared memory (its part of runs_b is then free: the
+            // merged list may grow over it)
+            const int np = min(max(__ldcg(a.chunk_cnt + g0 + c), 0), kZsChunk);
+            for (int t = tid; t < np; t += kThreads) {
+                const int4 q = __ldcg(rb + c * kZsChunk + t);
+                S.pc[t] = q.x;
+                S.ps[t] = __int_as_float(q.y);
             }
             __syncthreads();
-            zs_sort(S.key, S.val, n2);
-            zs_segsum(S.key, S.val, S.v2, S.f, S.f2, n2, 32);
-            for (int i = tid; i < n2; i += kThreads) {
-                const uint64_t k = S.key[i];
-                S.t[i] = (k != kZsPad && (i == n2 - 1 || (S.key[i + 1] >> 32) != (k >> 32))) ? 1u : 0u;
-            }
-            __syncthreads();
-            zs_scan_array(S.t, n2, S.s_warp);
-            const int np = (int)S.t[n2];
-            for (int i = tid; i < n2; i += kThreads) {
-                const uint64_t k = S.key[i];
-                if (k != kZsPad && (i == n2 - 1 || (S.key[i + 1] >> 32) != (k >> 32))) {
-                    S.pc[S.t[i]] = (int)(k >> 32);
-                    S.ps[S.t[i]] = S.val[i];
-                }
-            }
-            __syncthreads();
-            // ---- merge the chunk's runs into the row's list (classes ascending); a class in
-            // both keeps its place in the list and adds the chunk's sum after the earlier ones
+            // step c reads the list from one buffer and writes it to the other: runs_a after
+            // even steps, the front of the row's runs_b slice after odd ones
+            const int4 *cur = (c & 1) ? ra : rb;
+            int4 *nxt = (c & 1) ? rb : ra;
+            if (c == 0) na = 0;
             for (int t = tid; t < np; t += kThreads) {
                 const int lb = lower_bound_runs(cur, na, S.pc[t]);
                 S.lba[t] = lb;
@@ -385,9 +525,13 @@ __global__ void __launch_bounds__(kThreads) k_zs_long(const __grid_constant__ Sp
             __syncthreads();
             zs_scan_array(S.t, np, S.s_warp);
             const int nu = (int)S.t[np];
+            if (na + nu > T) {  // cannot happen: a list holds distinct classes of the row
+                if (tid == 0) atomicOr(a.status, kStInternal);
+                break;
+            }
             for (int i = tid; i < na; i += kThreads) {
                 const int4 ai = __ldcg(&cur[i]);
-                int lo = 0, hi = np;  // chunk runs with a smaller class
+                int lo = 0, hi = np;
                 while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
                     if (S.pc[mid] < ai.x) lo = mid + 1;
@@ -405,17 +549,13 @@ __global__ void __launch_bounds__(kThreads) k_zs_long(const __grid_constant__ Sp
                 if (S.t[t + 1] != S.t[t]) nxt[S.lba[t] + (int)S.t[t]] = make_int4(S.pc[t], __float_as_int(S.ps[t]), 0, 0);
             __syncthreads();
             na += nu;
-            int4 *tmp = cur;
-            cur = nxt;
-            nxt = tmp;
         }
-        if (cur != a.runs_a + p0 + r) {
-            for (int i = tid; i < na; i += kThreads) a.runs_a[p0 + r + i] = __ldcg(&cur[i]);
+        if (m > 0 && ((m - 1) & 1)) {  // the last step wrote the front of runs_b
+            for (int i = tid; i < na; i += kThreads) ra[i] = __ldcg(rb + i);
         }
         if (tid == 0) a.cnt[r] = na;
         __syncthreads();
     }
-    if (err) atomicOr(a.status, err);
 }
 
 // ---- the count scan ---------------------------------------------------------------------
@@ -492,22 +632,30 @@ cudaError_t configure_sparse_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_zs_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(ZsRowsSmem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_zs_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ZsLongSmem));
+    e = cudaFuncSetAttribute(k_zs_long_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ZsLongSmem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_zs_long_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ZsLongSmem));
 }
 
 int sparse_scan_tiles(int32_t N) { return (int)(((int64_t)N + kZsScanTile - 1) / kZsScanTile); }
 int64_t sparse_long_cap(int64_t E) { return E / (kZsWin + 1) + 1; }
+int64_t sparse_windows(int64_t E) { return E / kZsWin + 1; }
+int64_t sparse_chunk_cap(int64_t E) { return (E + sparse_long_cap(E)) / kZsChunk + sparse_long_cap(E) + 1; }
 
 cudaError_t launch_sparse(const SparseArgs &a, int sms, cudaStream_t st) {
     if (a.N <= 0) return cudaSuccess;
     const int64_t windows = a.E / kZsWin + 1;
+    k_zs_wstart<<<(unsigned)std::min<int64_t>(((int64_t)a.N + kThreads) / kThreads, (int64_t)sms * 16), kThreads, 0,
+                  st>>>(a, (int)windows);
     k_zs_rows<<<(unsigned)windows, kThreads, sizeof(ZsRowsSmem), st>>>(a);
-    k_zs_long<<<2 * sms, kThreads, sizeof(ZsLongSmem), st>>>(a);
+    k_zs_long_plan<<<1, kThreads, 0, st>>>(a);
+    k_zs_long_sort<<<3 * sms, kThreads, sizeof(ZsLongSmem), st>>>(a);
+    k_zs_long_merge<<<2 * sms, kThreads, sizeof(ZsLongSmem), st>>>(a);
     const int tiles = sparse_scan_tiles(a.N);
     k_zs_scan_tiles<<<tiles, kThreads, 0, st>>>(a);
     k_zs_scan_top<<<1, kThreads, 0, st>>>(a, tiles);
-    const int64_t warps = a.N;
-    const int blocks = (int)std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)sms * 8);
+    const int64_t warps = a.N;  // one warp per row
+    const int blocks = (int)std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)1 << 30);
     k_zs_write<<<blocks, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }

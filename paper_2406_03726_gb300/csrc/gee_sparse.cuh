@@ -25,7 +25,11 @@ struct SparseArgs {
     int32_t *long_list;      // [long_cap] rows with more entries than one window holds
     uint32_t *long_count;    // [1] zeroed
     uint32_t long_cap;
+    uint32_t *chunk_off;     // [long_cap + 1] first chunk of each listed row, total last
+    int32_t *chunk_cnt;      // [chunk_cap] runs of each chunk
+    uint32_t chunk_cap;
     uint32_t *tile_sum;      // [scan tiles + 1]
+    int32_t *wstart;         // [windows + 1] first row of each window of CSR positions
     // output
     int32_t *zrowptr;        // [N+1]
     int32_t *zcol;           // [zcap]
@@ -38,5 +42,7 @@ cudaError_t configure_sparse_kernels();
 cudaError_t launch_sparse(const SparseArgs &a, int sms, cudaStream_t st);
 int sparse_scan_tiles(int32_t N);
 int64_t sparse_long_cap(int64_t E);
+int64_t sparse_chunk_cap(int64_t E);
+int64_t sparse_windows(int64_t E);
 
 }  // namespace gee
