@@ -405,6 +405,18 @@ int gee_batch_plan_launch(gee_batch_plan *plan, void *stream, uint32_t *d_status
 int gee_batch_plan_launch_timed(gee_batch_plan *plan, void *stream, float *phase_ms);
 void gee_batch_plan_destroy(gee_batch_plan *plan);
 
+/* The batch's tuning fields, chosen by timing whole batch launches (plans captured as CUDA
+ * graphs, two replays per candidate): a coordinate search over vec_width {8, 4, 2},
+ * short_len {256, 64, 128} and rows_per_item {auto, 4, 16, 32}, each field keeping its
+ * fastest value.  In a batch the fields act by graph class: short_len on the graphs with
+ * K > 8, rows_per_item on those with K <= 8, vec_width on the whole product launch; split
+ * thresholds stay automatic per graph.  A field set in opts stays fixed.  The workspace
+ * (gee_batch_autotune_workspace_size bytes) is overwritten, and so are the graphs' Z;
+ * best receives the options (flags of opts), best_ms the mean time of its launch. */
+size_t gee_batch_autotune_workspace_size(const gee_graph *graphs, int32_t G, const gee_opts *opts);
+int gee_batch_autotune(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                       size_t workspace_bytes, void *stream, gee_opts *best, float *best_ms);
+
 /* ------------------------------------------------------------------------------------
  * Serving: continuous batching of embedding requests.
  *

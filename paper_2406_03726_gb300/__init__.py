@@ -18,6 +18,8 @@ from ._native import (  # noqa: F401
     gee_server_poll,
     gee_server_release,
     gee_server_submit,
+    gee_batch_autotune,
+    gee_batch_autotune_workspace_size,
     gee_batch_plan_create,
     gee_batch_plan_destroy,
     gee_batch_plan_launch,
@@ -186,6 +188,30 @@ def class_counts(rowptr, col, N, labels, K, stream=None):
     C = torch.empty((N, K), dtype=torch.int32, device=labels.device)
     _check(gee_class_counts(rowptr, col, N, labels, K, C, stream), "gee_class_counts")
     return C
+
+
+def batch_autotune(graphs, flags=0, stream=None):
+    """Tuning fields for a batch, by timing whole batch launches (gee_batch_autotune).
+    graphs: (src, dst, w, labels, N, K) device tensors as for BatchPlan; their Z is
+    scratch here.  Returns (gee_opts, ms per launch)."""
+    import ctypes
+    import torch
+    items, Zs = [], []
+    for (src, dst, w, labels, N, K) in graphs:
+        Z = torch.empty((N, K), dtype=torch.float32, device=labels.device)
+        Zs.append(Z)
+        items.append((src, dst, w, labels, Z, int(src.numel()), N, K))
+    arr = make_graphs(items)
+    o = make_opts(flags)
+    n = gee_batch_autotune_workspace_size(arr, len(items), o)
+    if n == 0:
+        raise GeeError(1, "gee_batch_autotune_workspace_size")
+    ws = torch.empty(n, dtype=torch.uint8, device=graphs[0][3].device)
+    best = make_opts(flags)
+    ms = ctypes.c_float(0.0)
+    _check(gee_batch_autotune(arr, len(items), o, ws, n, stream, best, ms), "gee_batch_autotune")
+    del ws, Zs
+    return best, float(ms.value)
 
 
 class BatchPlan:

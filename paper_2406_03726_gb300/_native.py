@@ -74,6 +74,8 @@ _SIGNATURES = {
     "gee_batch_plan_launch": ([_P, _P, _P, ctypes.c_int], ctypes.c_int),
     "gee_batch_plan_launch_timed": ([_P, _P, _P], ctypes.c_int),
     "gee_batch_plan_destroy": ([_P], None),
+    "gee_batch_autotune_workspace_size": ([_P, _I32, _P], _SZ),
+    "gee_batch_autotune": ([_P, _I32, _P, _P, _SZ, _P, _P, _P], ctypes.c_int),
     "gee_server_create": ([_P, _P], ctypes.c_int),
     "gee_server_submit": ([_P, _P, _P], ctypes.c_int),
     "gee_server_poll": ([_P, _I64, ctypes.c_int, _P, _P, _P], ctypes.c_int),
@@ -285,6 +287,15 @@ def make_graphs(items):
 
 def gee_batch_workspace_size(graphs, G, opts=None) -> int:
     return lib().gee_batch_workspace_size(graphs, G, _opts_ref(opts))
+
+
+def gee_batch_autotune_workspace_size(graphs, G, opts=None) -> int:
+    return lib().gee_batch_autotune_workspace_size(graphs, G, _opts_ref(opts))
+
+
+def gee_batch_autotune(graphs, G, opts, workspace, workspace_bytes, stream=None, best=None, best_ms=None) -> int:
+    return lib().gee_batch_autotune(graphs, G, _opts_ref(opts), ptr(workspace), workspace_bytes,
+                                    stream_handle(stream), ctypes.byref(best), ctypes.byref(best_ms))
 
 
 def gee_embed_batch(graphs, G, opts, workspace, workspace_bytes, stream=None, d_status=None) -> int:

@@ -1732,4 +1732,98 @@ void gee_batch_plan_destroy(gee_batch_plan *p) {
     delete p;
 }
 
+// The candidates of the batch tuner, around the automatic values (a field the caller set
+// stays fixed).  In a batch the fields act by graph class: short_len on the graphs with
+// K > 8 (their length buckets), rows_per_item on those with K <= 8 (their row blocks),
+// vec_width on the whole product launch; split thresholds stay per graph (automatic).
+static void batch_tune_axes(const gee_opts &o, std::vector<int32_t> (&ax)[3]) {
+    if (o.vec_width == 0) ax[0] = {8, 4, 2};
+    else ax[0] = {o.vec_width};
+    if (o.short_len == 0) ax[1] = {256, 64, 128};
+    else ax[1] = {o.short_len};
+    if (o.rows_per_item == 0) ax[2] = {0, 4, 16, 32};
+    else ax[2] = {o.rows_per_item};
+}
+
+size_t gee_batch_autotune_workspace_size(const gee_graph *graphs, int32_t G, const gee_opts *opts) {
+    const gee_opts o = gee::opts_or_default(opts);
+    std::vector<int32_t> ax[3];
+    batch_tune_axes(o, ax);
+    size_t m = 0;
+    for (int32_t v : ax[0])
+        for (int32_t sl : ax[1])
+            for (int32_t r : ax[2]) {
+                gee_opts c = o;
+                c.vec_width = v;
+                c.short_len = sl;
+                c.rows_per_item = r;
+                const size_t n = gee_batch_workspace_size(graphs, G, &c);
+                if (n == 0) return 0;
+                m = std::max(m, n);
+            }
+    return m;
+}
+
+int gee_batch_autotune(const gee_graph *graphs, int32_t G, const gee_opts *opts, void *d_workspace,
+                       size_t workspace_bytes, void *stream, gee_opts *best, float *best_ms) {
+    if (!best || G < 1) return GEE_ERR_ARG;
+    const gee_opts o = gee::opts_or_default(opts);
+    GEE_TRY(gee::check_opts(o));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GEE_TRY(gee::cuda_check(cudaEventCreate(&e0)));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GEE_ERR_CUDA;
+    }
+    // mean time of two replays (after one captured launch) of a plan with options c
+    auto time_of = [&](const gee_opts &c, float &ms) -> int {
+        ms = -1.0f;
+        if (gee_batch_workspace_size(graphs, G, &c) > workspace_bytes) return GEE_OK;
+        gee_batch_plan *plan = nullptr;
+        GEE_TRY(gee_batch_plan_create(graphs, G, &c, d_workspace, workspace_bytes, stream, &plan));
+        int rc = gee_batch_plan_launch(plan, stream, nullptr, 1);
+        if (rc == GEE_OK) rc = gee::cuda_check(cudaEventRecord(e0, st));
+        for (int i = 0; i < 2 && rc == GEE_OK; ++i) rc = gee_batch_plan_launch(plan, stream, nullptr, 1);
+        if (rc == GEE_OK) rc = gee::cuda_check(cudaEventRecord(e1, st));
+        if (rc == GEE_OK) rc = gee::cuda_check(cudaEventSynchronize(e1));
+        if (rc == GEE_OK) rc = gee::cuda_check(cudaEventElapsedTime(&ms, e0, e1));
+        gee_batch_plan_destroy(plan);
+        ms = rc == GEE_OK ? ms / 2.0f : -1.0f;
+        return rc;
+    };
+    std::vector<int32_t> ax[3];
+    batch_tune_axes(o, ax);
+    int32_t cur[3] = {ax[0][0], ax[1][0], ax[2][0]};
+    auto with = [&](const int32_t (&f)[3]) {
+        gee_opts c = o;
+        c.vec_width = f[0];
+        c.short_len = f[1];
+        c.rows_per_item = f[2];
+        return c;
+    };
+    float best_t = -1.0f;
+    int rc = time_of(with(cur), best_t);
+    for (int a = 0; a < 3 && rc == GEE_OK; ++a)
+        for (int32_t v : ax[a]) {
+            if (v == cur[a]) continue;
+            int32_t trial[3] = {cur[0], cur[1], cur[2]};
+            trial[a] = v;
+            float ms = -1.0f;
+            rc = time_of(with(trial), ms);
+            if (rc != GEE_OK) break;
+            if (ms >= 0.0f && (best_t < 0.0f || ms < best_t)) {
+                best_t = ms;
+                cur[a] = v;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GEE_OK) return rc;
+    if (best_t < 0.0f) return GEE_ERR_WORKSPACE;
+    *best = with(cur);
+    if (best_ms) *best_ms = best_t;
+    return GEE_OK;
+}
+
 }  // extern "C"

@@ -172,3 +172,34 @@ def test_full_4096_graph_batch_on_a_seeded_sample(gee):
     plan.close()
     del graphs, Zs
     torch.cuda.empty_cache()
+
+
+def test_batch_tuner_picks_candidates_that_keep_parity(gee):
+    """gee_batch_autotune: the chosen fields come from its candidate lists (a field set by
+    the caller stays fixed), and the tuned plan still matches the oracle graph by graph."""
+    graphs = small_mix(24, seed=45)
+    assert any(g.K > 8 for g in graphs) and any(g.K <= 8 for g in graphs)
+    dg = [dev_graph(g) for g in graphs]
+    items = [(s, d, w, y, g.N, g.K) for (s, d, w, y), g in zip(dg, graphs)]
+    best, ms = gee.batch_autotune(items, ALL)
+    assert ms > 0.0 and best.flags == ALL
+    assert best.vec_width in (2, 4, 8) and best.short_len in (64, 128, 256)
+    assert best.rows_per_item in (0, 4, 16, 32) and best.hub_threshold == 0
+    plan = gee.BatchPlan(items, opts=best)
+    Zs = plan.launch(use_graph=True)
+    torch.cuda.synchronize()
+    assert int(plan.status.abs().sum().item()) == 0
+    for g, Zb in zip(graphs, Zs):
+        assert_z_matches(Zb.double().cpu().numpy(), oracle.embed_graph(g, ALL), what=g.name)
+    plan.close()
+    # a field given by the caller is not searched
+    fixed = gee.make_opts(ALL, 0, 0, 0, 2, 0)
+    import ctypes
+    from paper_2406_03726_gb300 import _native as nat
+    Zkeep = [torch.empty((g.N, g.K), device="cuda") for g in graphs]   # outlive the tuner's launches
+    arr = nat.make_graphs([(s, d, w, y, Z, g.E, g.N, g.K) for (s, d, w, y), g, Z in zip(dg, graphs, Zkeep)])
+    n = gee.gee_batch_autotune_workspace_size(arr, len(graphs), fixed)
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    out, t = gee.make_opts(ALL), ctypes.c_float(0.0)
+    assert gee.gee_batch_autotune(arr, len(graphs), fixed, ws, n, None, out, t) == 0
+    assert out.vec_width == 2
