@@ -1403,7 +1403,7 @@ void plan_sparse(const Shape &s, const gee_opts &o, char *base, SinglePlan &p, S
     a.cnt = b.take<int32_t>((size_t)N);
     a.long_cap = (uint32_t)sparse_long_cap(E);
     a.long_list = b.take<int32_t>(a.long_cap);
-    a.long_count = b.take<uint32_t>(1);
+    a.long_count = b.take<uint32_t>(2);
     a.chunk_cap = (uint32_t)sparse_chunk_cap(E);
     a.chunk_off = b.take<uint32_t>((size_t)a.long_cap + 1);
     a.chunk_cnt = b.take<int32_t>(a.chunk_cap);
@@ -1477,7 +1477,7 @@ int gee_embed_sparse(const int32_t *d_src, const int32_t *d_dst, const float *d_
     a.zval = d_zval;
     a.zcap = zcap;
     a.status = d.status;
-    GEE_TRY(cuda_check(cudaMemsetAsync(a.long_count, 0, sizeof(uint32_t), st)));
+    GEE_TRY(cuda_check(cudaMemsetAsync(a.long_count, 0, 2 * sizeof(uint32_t), st)));
     GEE_TRY(cuda_check(launch_sparse(a, dev.sms, st)));
     if (d_status)
         GEE_TRY(cuda_check(cudaMemcpyAsync(d_status, d.status, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)));

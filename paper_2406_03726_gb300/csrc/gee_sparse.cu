@@ -16,9 +16,9 @@
 //               (a fixed tree per window, so the bits are reproducible), and writes each
 //               row's runs to its own slice of the run buffer, at rowptr[i] + i.  Empty
 //               rows get their augmentation term; longer rows are listed.
-//   k_zs_long   one CTA per listed row: chunks of kZsChunk entries are sorted and summed
-//               the same way, and merged into the row's sorted run list in chunk order
-//               (sums with two-sum compensation).
+//   k_zs_long_* the listed rows' chunks of kZsChunk entries are sorted and summed the
+//               same way by any CTA; then one CTA per row merges its chunk lists into the
+//               row's sorted run list in chunk order (sums with two-sum compensation).
 //   k_zs_scan*  exclusive scan of the per-row run counts -> zrowptr.
 //   k_zs_write  one warp per row: D_ii^-1/2, the row norm, and the stores.
 #include "gee_internal.cuh"
@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kZsWin = 1024;                  // window of CSR positions per k_zs_rows CTA
 constexpr int kZsTile = 3 * kZsWin;           // entries a window can hold (at most 3 kZsWin - 1)
-constexpr int kZsChunk = 2048;                // entries per chunk of a long row
+constexpr int kZsChunk = 4096;                // entries per chunk of a long row
 constexpr int kZsScanTile = 2048;             // rows per tile of the count scan
 constexpr uint32_t kZsNoClass = 0x1fffffu;    // class field of an unlabelled neighbour
 constexpr uint64_t kZsPad = ~0ull;
@@ -67,9 +67,9 @@ __device__ __forceinline__ uint32_t zs_block_scan(uint32_t v, uint32_t *s_warp, 
     return before + x - v;
 }
 
-// Exclusive scan of n <= 16 * 256 flags in place (t[0..n) -> prefix; t[n] = total).
+// Exclusive scan of n <= kPer * 256 flags in place (t[0..n) -> prefix; t[n] = total).
+template <int kPer = 16>
 __device__ void zs_scan_array(uint32_t *t, int n, uint32_t *s_warp) {
-    constexpr int kPer = 16;
     const int i0 = threadIdx.x * kPer;
     uint32_t loc[kPer];
     uint32_t sum = 0;
@@ -396,22 +396,30 @@ __global__ void __launch_bounds__(kThreads) k_zs_long_plan(const __grid_constant
     if (threadIdx.x == 0 && run > a.chunk_cap) atomicOr(a.status, kStInternal);
 }
 
-struct ZsLongSmem {
+struct ZsLongSortSmem {
     uint64_t key[kZsChunk];
     float val[kZsChunk];
-    float v2[kZsChunk];
-    uint32_t t[kZsChunk + 1];     // tail flags and their scan; unmatched flags and their scan
+    union {                       // the segmented sum's scratch, then the tail flags and
+        float v2[kZsChunk + 1];   // their exclusive scan
+        uint32_t t[kZsChunk + 1];
+    };
     uint8_t f[kZsChunk], f2[kZsChunk];
+    uint32_t s_warp[kWarps];
+    int32_t s_li;
+};
+
+struct ZsLongMergeSmem {
     int32_t pc[kZsChunk];         // a chunk's runs: class, sum
     float ps[kZsChunk];
     int32_t lba[kZsChunk];        // for each run: the runs of the list with a smaller class
+    uint32_t t[kZsChunk + 1];     // unmatched flags, then their exclusive scan
     uint32_t s_warp[kWarps];
     int32_t s_li;
 };
 
 __global__ void __launch_bounds__(kThreads) k_zs_long_sort(const __grid_constant__ SparseArgs a) {
     extern __shared__ __align__(16) unsigned char zs_smem[];
-    ZsLongSmem &S = *reinterpret_cast<ZsLongSmem *>(zs_smem);
+    ZsLongSortSmem &S = *reinterpret_cast<ZsLongSortSmem *>(zs_smem);
     const int tid = threadIdx.x;
     const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
     const uint32_t chunks = n ? __ldcg(a.chunk_off + n) : 0u;
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) k_zs_long_sort(const __grid_constant
             S.t[i] = (k != kZsPad && (i == n2 - 1 || (S.key[i + 1] >> 32) != (k >> 32))) ? 1u : 0u;
         }
         __syncthreads();
-        zs_scan_array(S.t, n2, S.s_warp);
+        zs_scan_array<kZsChunk / kThreads>(S.t, n2, S.s_warp);
         int4 *out = a.runs_b + p0 + r + c0;  // the chunk's own part of the row's slice
         for (int i = tid; i < n2; i += kThreads) {
             const uint64_t k = S.key[i];
@@ -487,10 +495,14 @@ __device__ __forceinline__ int lower_bound_runs(const int4 *A, int n, int c) {
 
 __global__ void __launch_bounds__(kThreads) k_zs_long_merge(const __grid_constant__ SparseArgs a) {
     extern __shared__ __align__(16) unsigned char zs_smem[];
-    ZsLongSmem &S = *reinterpret_cast<ZsLongSmem *>(zs_smem);
+    ZsLongMergeSmem &S = *reinterpret_cast<ZsLongMergeSmem *>(zs_smem);
     const int tid = threadIdx.x;
     const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
-    for (uint32_t li = blockIdx.x; li < n; li += gridDim.x) {
+    for (;;) {
+        if (tid == 0) S.s_li = (int32_t)atomicAdd(a.long_count + 1, 1u);  // rows claimed one at a time
+        __syncthreads();
+        const uint32_t li = (uint32_t)S.s_li;
+        if (li >= n) break;
         const int r = min(max(__ldcg(a.long_list + li), 0), a.N - 1);
         int64_t p0;
         const int T = long_row_entries(a, r, p0);
@@ -523,7 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_zs_long_merge(const __grid_constan
                 S.t[t] = (lb < na && __ldcg(&cur[lb].x) == S.pc[t]) ? 0u : 1u;  // unmatched
             }
             __syncthreads();
-            zs_scan_array(S.t, np, S.s_warp);
+            zs_scan_array<kZsChunk / kThreads>(S.t, np, S.s_warp);
             const int nu = (int)S.t[np];
             if (na + nu > T) {  // cannot happen: a list holds distinct classes of the row
                 if (tid == 0) atomicOr(a.status, kStInternal);
@@ -626,15 +638,16 @@ __global__ void __launch_bounds__(kThreads) k_zs_write(const __grid_constant__ S
 }  // namespace
 
 size_t sparse_smem_rows() { return sizeof(ZsRowsSmem); }
-size_t sparse_smem_long() { return sizeof(ZsLongSmem); }
 
 cudaError_t configure_sparse_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_zs_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(ZsRowsSmem));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_zs_long_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ZsLongSmem));
+    e = cudaFuncSetAttribute(k_zs_long_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ZsLongSortSmem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_zs_long_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ZsLongSmem));
+    return cudaFuncSetAttribute(k_zs_long_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(ZsLongMergeSmem));
 }
 
 int sparse_scan_tiles(int32_t N) { return (int)(((int64_t)N + kZsScanTile - 1) / kZsScanTile); }
@@ -649,8 +662,8 @@ cudaError_t launch_sparse(const SparseArgs &a, int sms, cudaStream_t st) {
                   st>>>(a, (int)windows);
     k_zs_rows<<<(unsigned)windows, kThreads, sizeof(ZsRowsSmem), st>>>(a);
     k_zs_long_plan<<<1, kThreads, 0, st>>>(a);
-    k_zs_long_sort<<<3 * sms, kThreads, sizeof(ZsLongSmem), st>>>(a);
-    k_zs_long_merge<<<2 * sms, kThreads, sizeof(ZsLongSmem), st>>>(a);
+    k_zs_long_sort<<<3 * sms, kThreads, sizeof(ZsLongSortSmem), st>>>(a);
+    k_zs_long_merge<<<2 * sms, kThreads, sizeof(ZsLongMergeSmem), st>>>(a);
     const int tiles = sparse_scan_tiles(a.N);
     k_zs_scan_tiles<<<tiles, kThreads, 0, st>>>(a);
     k_zs_scan_top<<<1, kThreads, 0, st>>>(a, tiles);

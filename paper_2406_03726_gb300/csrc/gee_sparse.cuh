@@ -23,7 +23,7 @@ struct SparseArgs {
     int32_t *cnt;            // [N] runs (distinct classes) per row
     int4 *runs_a, *runs_b;   // [E + N] {class, sum, compensation, 0}: row i at rowptr[i] + i
     int32_t *long_list;      // [long_cap] rows with more entries than one window holds
-    uint32_t *long_count;    // [1] zeroed
+    uint32_t *long_count;    // [2] zeroed: rows listed, rows claimed by the merge
     uint32_t long_cap;
     uint32_t *chunk_off;     // [long_cap + 1] first chunk of each listed row, total last
     int32_t *chunk_cnt;      // [chunk_cap] runs of each chunk

@@ -54,12 +54,12 @@ def test_sparse_tiny_all_options(seed):
 
 @pytest.mark.parametrize("K", [3, 64, 5000, 200000])
 def test_sparse_long_rows_split_in_chunks(K):
-    """Hub rows of up to ~20,000 entries: the window path and the chunk-merge path (rows
-    above 1024 entries, several 2048-entry chunks each)."""
+    """Hub rows of up to ~27,000 entries: the window path, single-chunk long rows (1024 to
+    4096 entries) and the chunk-merge path (rows of up to seven 4096-entry chunks)."""
     import paper_2406_03726_gb300 as gee
-    g = _relabel(chung_lu(40000, 400000, d_max=20000, seed=131, weighted=True), K, 132)
+    g = _relabel(chung_lu(100000, 1500000, d_max=60000, seed=131, weighted=True), K, 132)
     deg = np.bincount(g.src, minlength=g.N)
-    assert int((deg > 1024).sum()) >= 10 and int(deg.max()) > 3 * 2048
+    assert int((deg > 1024).sum()) >= 100 and int((deg > 4096).sum()) >= 10 and int(deg.max()) > 3 * 4096
     for flags in (0, ALL, 2, 5):
         _check(gee, g, flags, f"chung-lu K={K}")
 
