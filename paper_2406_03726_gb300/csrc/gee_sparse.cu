@@ -9,13 +9,15 @@
 // row) and zval.
 //
 // The CSR, degrees and node table come from the usual build.  Then:
-//   k_zs_rows   one CTA per window of kZsWin CSR positions takes the rows that start in
-//               it and have at most kZsWin entries (at most 3 kZsWin entries with the
-//               augmentation terms): it sorts the entries by (row, class, position) in
-//               shared memory (bitonic), sums each (row, class) run with a segmented scan
-//               (a fixed tree per window, so the bits are reproducible), and writes each
-//               row's runs to its own slice of the run buffer, at rowptr[i] + i.  Empty
-//               rows get their augmentation term; longer rows are listed.
+//   k_zs_wstart the first row of every window of kZsWin CSR positions.
+//   k_zs_rows   one CTA per window takes the rows that start in it and have at most
+//               kZsWin entries (at most 3 kZsWin - 1 entries with the augmentation terms):
+//               it loads them with every thread, sorts each row's entries by (class,
+//               position) in shared memory (a warp-level bitonic network per row), sums
+//               each (row, class) run with a segmented scan (a fixed tree per window, so
+//               the bits are reproducible), and writes each row's runs to its own slice of
+//               the run buffer, at rowptr[i] + i.  Empty rows get their augmentation
+//               term; longer rows are listed.
 //   k_zs_long_* the listed rows' chunks of kZsChunk entries are sorted and summed the
 //               same way by any CTA; then one CTA per row merges its chunk lists into the
 //               row's sorted run list in chunk order (sums with two-sum compensation).
@@ -637,7 +639,6 @@ __global__ void __launch_bounds__(kThreads) k_zs_write(const __grid_constant__ S
 
 }  // namespace
 
-size_t sparse_smem_rows() { return sizeof(ZsRowsSmem); }
 
 cudaError_t configure_sparse_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_zs_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
