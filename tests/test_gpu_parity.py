@@ -125,6 +125,28 @@ def test_chung_lu_600k_all_options(gee, cl600k):
     assert np.all((np.abs(r - 1) < 1e-5) | (r == 0))
 
 
+def _tuned(gee, g):
+    """The options bench.py times: the autotuner's choice for this graph, all options."""
+    src, dst, w, y = dev_graph(g)
+    opts, ms = gee.autotune(src, dst, w, g.N, y, g.K, ALL)
+    assert ms > 0.0
+    return opts
+
+
+@pytest.mark.parametrize("name", ["sbm2k", "sbm10k", "cl600k"])
+def test_bench_workloads_in_the_tuned_launch_configuration(gee, cl600k, name):
+    """Each single-graph workload of the benchmark, embedded with the tuning fields the
+    benchmark times (the split threshold and the short-row bound move rows between paths,
+    so they change the rounding), against the oracle entry by entry."""
+    g = {"sbm2k": lambda: sbm(2000, seed=1), "sbm10k": lambda: sbm(10000, seed=2, weighted=True),
+         "cl600k": lambda: cl600k}[name]()
+    opts = _tuned(gee, g)
+    Zg, st = run(gee, g, ALL, opts=opts)
+    assert st == 0
+    assert_z_matches(Zg, oracle.embed_graph(g, ALL), what=f"{name} tuned {opts.hub_threshold},"
+                                                           f"{opts.vec_width},{opts.short_len}")
+
+
 def test_chung_lu_600k_csr_and_degrees(gee, cl600k):
     g = cl600k
     src, dst, w, y = dev_graph(g)
