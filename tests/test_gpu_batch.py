@@ -174,7 +174,7 @@ def test_full_4096_graph_batch_on_a_seeded_sample(gee):
         g = Graph(s, d, w, y, specs[i]["N"], specs[i]["K"])
         assert_z_matches(Zs[i].double().cpu().numpy(), oracle.embed_graph(g, ALL), what=f"graph {i}")
     plan.close()
-    del graphs, Zs
+    del graphs, Zs, items
     torch.cuda.empty_cache()
 
 
