@@ -72,6 +72,29 @@ def test_argument_errors_need_no_gpu(lib):
     assert gee.gee_shard_workspace_size(100, 50, 0, 20, 3, False, gee.make_opts(7 | gee.SYMMETRIZE)) == 0
 
 
+def test_sparse_and_batch_tuner_host_checks(lib):
+    import paper_2406_03726_gb300 as gee
+    from paper_2406_03726_gb300 import _native as nat
+    o = gee.make_opts(7)
+    # sparse Z: K up to 2^20 classes, the usual N and E limits
+    assert gee.gee_sparse_workspace_size(1000, 100, 1 << 20, False, o) > 0
+    assert gee.gee_sparse_workspace_size(1000, 100, (1 << 20) + 1, False, o) == 0
+    assert gee.gee_sparse_workspace_size(1000, (1 << 21) + 1, 5, False, o) == 0
+    assert gee.gee_sparse_workspace_size(1000, 100, 0, False, o) == 0
+    # the workspace holds the CSR build plus two run buffers of E + N entries
+    assert gee.gee_sparse_workspace_size(10_000, 500, 7, True, o) > gee.gee_workspace_size(10_000, 500, 7, True, o)
+    # too little room for Z's entries (E + N) is refused before any CUDA call
+    assert gee.gee_embed_sparse(1, 1, None, 40, 10, 1, 3, o, 1, 1, 1, 49, 1, 1 << 20) == 1
+    assert gee.gee_embed_sparse(1, 1, None, 40, 10, 1, 3, gee.make_opts(7 | gee.SYMMETRIZE), 1, 1, 1, 89, 1,
+                                1 << 20) == 1
+    # the batch tuner's workspace covers every candidate plan
+    graphs = (nat.gee_graph * 2)()
+    graphs[0] = nat.gee_graph(1, 1, 1, 1, 1, 5000, 300, 20)
+    graphs[1] = nat.gee_graph(1, 1, None, 1, 1, 800, 90, 4)
+    base = gee.gee_batch_workspace_size(graphs, 2, o)
+    assert base > 0 and gee.gee_batch_autotune_workspace_size(graphs, 2, o) >= base
+
+
 def test_tuning_fields_checked_on_host(lib):
     import paper_2406_03726_gb300 as gee
     # rows_per_item and lanes_per_row must be powers of two up to 32
