@@ -837,6 +837,17 @@ def gpu_arm(args):
     return 0
 
 
+def sparse_only(args):
+    """The sparse-Z record of one workload (one GPU), as one JSON line."""
+    import torch
+    import paper_2406_03726_gb300 as gee
+    dev = torch.device("cuda", 0)
+    g = make_graph(args.workload)
+    rec = measure_sparse(gee, g, dev, args.steps, args.sparse_k)
+    print(json.dumps({"workload": WORKLOADS[args.workload]["desc"], "sparse": rec}))
+    return 0
+
+
 def gee_phase_count():
     return 16  # room for the GEE_NUM_PHASES floats gee_embed_timed writes
 
@@ -904,9 +915,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the sub-records of the other workloads")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--sparse-k", type=int, default=0,
+                    help="only the sparse-Z measurement of the workload, with labels drawn from this many "
+                         "classes (profiling runs)")
     ap.add_argument("--opts", default="", help="hub_threshold,rows_per_item,vec_width,short_len for the main "
                                                 "workload instead of the autotuner (profiling runs)")
     args = ap.parse_args()
+    if args.sparse_k:
+        return sparse_only(args)
     if args.impl == "reference":
         if args.workload in ("batch", "serve"):
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single graphs only"}))
