@@ -411,12 +411,13 @@ struct ZsLongSortSmem {
 };
 
 struct ZsLongMergeSmem {
-    int32_t pc[kZsChunk];         // a chunk's runs: class, sum
-    float ps[kZsChunk];
-    int32_t lba[kZsChunk];        // for each run: the runs of the list with a smaller class
-    uint32_t t[kZsChunk + 1];     // unmatched flags, then their exclusive scan
+    uint32_t hist[kWarps][256];   // per-warp digit counts of a radix pass
+    uint32_t wpre[kWarps][256];   // per tile: each warp's first place among a digit's elements
+    uint16_t cnt[kWarps][256];    // per tile: each warp's elements of a digit so far
+    uint32_t base[256];           // next place of each digit in the pass's output
     uint32_t s_warp[kWarps];
     int32_t s_li;
+    uint32_t s_carry;
 };
 
 __global__ void __launch_bounds__(kThreads) k_zs_long_sort(const __grid_constant__ SparseArgs a) {
@@ -485,21 +486,17 @@ __global__ void __launch_bounds__(kThreads) k_zs_long_sort(const __grid_constant
     }
 }
 
-__device__ __forceinline__ int lower_bound_runs(const int4 *A, int n, int c) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldcg(&A[mid].x) < c) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
+// One listed row per CTA (rows claimed one at a time): the row's chunk lists, each sorted by
+// class, are concatenated in chunk order, sorted by class with a stable radix sort (8-bit
+// digits; a class's entries stay in chunk order), and each run of one class is summed in
+// that order with two-sum compensation.  Work and traffic are linear in the row's runs.
 __global__ void __launch_bounds__(kThreads) k_zs_long_merge(const __grid_constant__ SparseArgs a) {
     extern __shared__ __align__(16) unsigned char zs_smem[];
     ZsLongMergeSmem &S = *reinterpret_cast<ZsLongMergeSmem *>(zs_smem);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const uint32_t n = min(__ldcg(a.long_count), a.long_cap);
+    const int bits = 32 - __clz((unsigned)max(a.K - 1, 1));  // class bits
     for (;;) {
         if (tid == 0) S.s_li = (int32_t)atomicAdd(a.long_count + 1, 1u);  // rows claimed one at a time
         __syncthreads();
@@ -510,63 +507,98 @@ __global__ void __launch_bounds__(kThreads) k_zs_long_merge(const __grid_constan
         const int T = long_row_entries(a, r, p0);
         const uint32_t g0 = __ldcg(a.chunk_off + li), g1 = __ldcg(a.chunk_off + li + 1);
         int4 *const ra = a.runs_a + p0 + r, *const rb = a.runs_b + p0 + r;
-        int na = 0;
-        // chunk numbers beyond the capacity (reported by the plan) or more chunks than
-        // the row's entries give: skip the row
+        // chunk numbers beyond the capacity (reported by the plan) or more chunks than the
+        // row's entries give: skip the row
         const bool ok = g0 <= g1 && g1 <= a.chunk_cap &&
                         (int64_t)(g1 - g0) <= ((int64_t)T + kZsChunk - 1) / kZsChunk;
         const int m = ok ? (int)(g1 - g0) : 0;
+        // ---- the chunk lists, concatenated in chunk order, into runs_a
+        int M = 0;
         for (int c = 0; c < m; ++c) {
-            // the chunk's runs into shared memory (its part of runs_b is then free: the
-            // merged list may grow over it)
             const int np = min(max(__ldcg(a.chunk_cnt + g0 + c), 0), kZsChunk);
-            for (int t = tid; t < np; t += kThreads) {
-                const int4 q = __ldcg(rb + c * kZsChunk + t);
-                S.pc[t] = q.x;
-                S.ps[t] = __int_as_float(q.y);
-            }
-            __syncthreads();
-            // step c reads the list from one buffer and writes it to the other: runs_a after
-            // even steps, the front of the row's runs_b slice after odd ones
-            const int4 *cur = (c & 1) ? ra : rb;
-            int4 *nxt = (c & 1) ? rb : ra;
-            if (c == 0) na = 0;
-            for (int t = tid; t < np; t += kThreads) {
-                const int lb = lower_bound_runs(cur, na, S.pc[t]);
-                S.lba[t] = lb;
-                S.t[t] = (lb < na && __ldcg(&cur[lb].x) == S.pc[t]) ? 0u : 1u;  // unmatched
-            }
-            __syncthreads();
-            zs_scan_array<kZsChunk / kThreads>(S.t, np, S.s_warp);
-            const int nu = (int)S.t[np];
-            if (na + nu > T) {  // cannot happen: a list holds distinct classes of the row
-                if (tid == 0) atomicOr(a.status, kStInternal);
-                break;
-            }
-            for (int i = tid; i < na; i += kThreads) {
-                const int4 ai = __ldcg(&cur[i]);
-                int lo = 0, hi = np;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (S.pc[mid] < ai.x) lo = mid + 1;
-                    else hi = mid;
-                }
-                float s = __int_as_float(ai.y), comp = __int_as_float(ai.z);
-                if (lo < np && S.pc[lo] == ai.x) {
-                    const float2 q = two_sum2(s, S.ps[lo]);
-                    s = q.x;
-                    comp += q.y;
-                }
-                nxt[i + (int)S.t[lo]] = make_int4(ai.x, __float_as_int(s), __float_as_int(comp), 0);
-            }
-            for (int t = tid; t < np; t += kThreads)
-                if (S.t[t + 1] != S.t[t]) nxt[S.lba[t] + (int)S.t[t]] = make_int4(S.pc[t], __float_as_int(S.ps[t]), 0, 0);
-            __syncthreads();
-            na += nu;
+            for (int t = tid; t < np; t += kThreads) ra[M + t] = __ldcg(rb + c * kZsChunk + t);
+            M += np;
         }
-        if (m > 0 && ((m - 1) & 1)) {  // the last step wrote the front of runs_b
-            for (int i = tid; i < na; i += kThreads) ra[i] = __ldcg(rb + i);
+        __syncthreads();
+        // ---- stable radix sort by class, runs_a <-> runs_b
+        int4 *src = ra, *dst = rb;
+        for (int sh = 0; sh < bits; sh += 8) {
+            for (int i = tid; i < kWarps * 256; i += kThreads) (&S.hist[0][0])[i] = 0u;
+            __syncthreads();
+            for (int i = tid; i < M; i += kThreads) atomicAdd(&S.hist[warp][(__ldcg(&src[i].x) >> sh) & 255], 1u);
+            __syncthreads();
+            {  // digit bases: exclusive scan of the digit totals (thread = digit)
+                uint32_t tot = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) tot += S.hist[w][tid];
+                uint32_t all;
+                S.base[tid] = zs_block_scan(tot, S.s_warp, all);
+            }
+            __syncthreads();
+            for (int t0 = 0; t0 < M; t0 += kThreads * 8) {
+                for (int i = lane; i < 256; i += 32) S.cnt[warp][i] = 0;
+                __syncwarp();
+                int4 el[8];
+                uint32_t dg[8], rk[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {  // element t0 + 256 warp + 32 u + lane: tile order kept
+                    const int idx = t0 + warp * 256 + u * 32 + lane;
+                    const bool valid = idx < M;
+                    el[u] = valid ? __ldcg(&src[idx]) : make_int4(0, 0, 0, 0);
+                    dg[u] = valid ? ((uint32_t)el[u].x >> sh) & 255u : 256u + (uint32_t)lane;  // unique if invalid
+                    const unsigned peers = __match_any_sync(0xffffffffu, dg[u]);
+                    const uint32_t before = valid ? S.cnt[warp][dg[u]] : 0u;
+                    __syncwarp();
+                    if (valid && (peers & lt) == 0u) S.cnt[warp][dg[u]] = (uint16_t)(before + __popc(peers));
+                    __syncwarp();
+                    rk[u] = before + __popc(peers & lt);
+                }
+                __syncthreads();
+                uint32_t tile_tot = 0;  // thread = digit: each warp's first place in the tile
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    S.wpre[w][tid] = tile_tot;
+                    tile_tot += S.cnt[w][tid];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (dg[u] < 256u) dst[S.base[dg[u]] + S.wpre[warp][dg[u]] + rk[u]] = el[u];
+                __syncthreads();
+                S.base[tid] += tile_tot;
+                __syncthreads();
+            }
+            int4 *tmp = src;
+            src = dst;
+            dst = tmp;
         }
+        // ---- one run per class (in chunk order): its sum into dst, then dst -> runs_a
+        if (tid == 0) S.s_carry = 0;
+        __syncthreads();
+        for (int t0 = 0; t0 < M; t0 += kThreads) {
+            const int i = t0 + tid;
+            const bool head = i < M && (i == 0 || __ldcg(&src[i].x) != __ldcg(&src[i - 1].x));
+            uint32_t tot;
+            const uint32_t x = zs_block_scan(head ? 1u : 0u, S.s_warp, tot);
+            if (head) {
+                const int4 h = __ldcg(&src[i]);
+                float sum = __int_as_float(h.y), comp = __int_as_float(h.z);
+                for (int j = i + 1; j < M; ++j) {
+                    const int4 q = __ldcg(&src[j]);
+                    if (q.x != h.x) break;
+                    const float2 t = two_sum2(sum, __int_as_float(q.y));
+                    sum = t.x;
+                    comp += t.y + __int_as_float(q.z);
+                }
+                dst[S.s_carry + x] = make_int4(h.x, __float_as_int(sum), __float_as_int(comp), 0);
+            }
+            __syncthreads();
+            if (tid == 0) S.s_carry += tot;
+            __syncthreads();
+        }
+        const int na = (int)S.s_carry;
+        if (dst != ra)
+            for (int i = tid; i < na; i += kThreads) ra[i] = __ldcg(dst + i);
         if (tid == 0) a.cnt[r] = na;
         __syncthreads();
     }
