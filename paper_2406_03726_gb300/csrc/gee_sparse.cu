@@ -19,8 +19,9 @@
 //               the run buffer, at rowptr[i] + i.  Empty rows get their augmentation
 //               term; longer rows are listed.
 //   k_zs_long_* the listed rows' chunks of kZsChunk entries are sorted and summed the
-//               same way by any CTA; then one CTA per row merges its chunk lists into the
-//               row's sorted run list in chunk order (sums with two-sum compensation).
+//               same way by any CTA; then one CTA per row concatenates its chunk lists in
+//               chunk order, sorts them by class with a stable radix sort and sums each
+//               class's partial sums in chunk order (two-sum compensation).
 //   k_zs_scan*  exclusive scan of the per-row run counts -> zrowptr.
 //   k_zs_write  one warp per row: D_ii^-1/2, the row norm, and the stores.
 #include "gee_internal.cuh"
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_zs_rows(const __grid_constant__ Sp
 // A listed row of T = len (+1 augmentation term) entries has ceil(T / kZsChunk) chunks.
 // k_zs_long_plan numbers the chunks of all listed rows; k_zs_long_sort sorts and sums each
 // chunk (any CTA) into its sorted run list, stored in the row's slice of runs_b at
-// c * kZsChunk; k_zs_long_merge merges a row's chunk lists in chunk order (one CTA per row).
+// c * kZsChunk; k_zs_long_merge combines a row's chunk lists (one CTA per row).
 
 __device__ __forceinline__ int long_row_entries(const SparseArgs &a, int r, int64_t &p0) {
     p0 = __ldg(a.rowptr + r);
