@@ -527,6 +527,8 @@ constexpr size_t kStageBytes = (size_t)3 * kStreamWords * 4;  // src|tmpk, dst, 
 constexpr size_t kTileBytes = (size_t)3 * kSortTile * 4;      // sorted pos, payload, weight
 constexpr int kSepDigits = 512;                               // wcnt apart from the tile up to here
 constexpr int kBinDigits = 256;                               // peer-mask entries per warp
+constexpr int kScatterCols = kMaxDigits / 2 / kThreads;       // digit pairs per thread, at most
+static_assert(kScatterCols * kWarps <= 32, "column-warp totals are scanned by one warp");
 
 __host__ __device__ constexpr size_t scatter_wcnt_bytes(int D) { return (size_t)D * kWarps * 2; }
 __host__ __device__ constexpr size_t scatter_union_bytes(int D) {
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const __grid_constant__
     __shared__ GraphDesc sg;
     __shared__ int sl[2];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t s_scan[kScatterCols * kWarps];
     __shared__ uint32_t s_err;
     __shared__ int s_staged;
 
@@ -637,9 +639,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const __grid_constant__
     uint32_t *bins = run + D;  // [kWarps][BD]
     uint16_t *mycnt = wcnt + warp * D;
     uint32_t *mybins = bins + warp * BD;
-
-    const int dpt = (D + kThreads - 1) / kThreads;
-    const int dlo = min(D, tid * dpt), dhi = min(D, dlo + dpt);
+    // per-digit work by digit pairs (D >= 2): thread t owns pairs p = t + kThreads j, j <
+    // ppt, so a warp's accesses to the per-digit arrays are consecutive words
+    const int P = D >> 1;
+    const int ppt = (P + kThreads - 1) / kThreads;  // <= kScatterCols
+    uint32_t *wc32 = reinterpret_cast<uint32_t *>(wcnt);  // [kWarps][P]: two u16 counters
+    uint2 *tstart2 = reinterpret_cast<uint2 *>(tstart);
+    uint2 *dglob2 = reinterpret_cast<uint2 *>(dglob);
+    uint2 *run2 = reinterpret_cast<uint2 *>(run);
     // virtual entries of the range (a tile is kSortTile of them); with symmetrizing, the
     // COO pass reads input edge v >> 1 for entry v
     const int sh = coo ? vshift(sg) : 0;
@@ -654,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const __grid_constant__
         s_staged = scatter_issue_stage<FINAL>(sg, r0 >> sh, min(rn, kSortTile) >> sh, stage, &bar);
     }
     for (int i = tid; i < kWarps * BD; i += kThreads) bins[i] = 0u;
-    for (int d = dlo; d < dhi; ++d) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
+    for (int d = tid; d < D; d += kThreads) run[d] = __ldcg(offs + ((size_t)r << bits) + d);
     __syncthreads();
     uint32_t parity = 0;
     const unsigned lt = lanemask_lt();
@@ -753,47 +760,59 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const __grid_constant__
         }
         __syncthreads();  // B
 
-        // ---- per digit: warp offsets, tile counts, tile-local starts, global positions
-        uint32_t tcount[8];  // counts of the owned digits (dpt <= 8)
-        uint32_t loc = 0, nranked = 0;  // nranked: the tile's ranked elements (dropped ones are not)
+        // ---- per digit: warp offsets, tile counts, tile-local starts, global positions.
+        // The tile-local starts follow the digit order, which is the order (j, t) of the
+        // owned pairs: a warp scan per column j, then a scan of the column-warp totals.
+        uint32_t c0[kScatterCols], c1[kScatterCols], xs[kScatterCols];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int d = dlo + j;
-            uint32_t sum = 0;
-            if (d < dhi) {
+        for (int j = 0; j < kScatterCols; ++j) {
+            const int p = tid + j * kThreads;
+            uint32_t s0 = 0, s1 = 0;
+            if (j < ppt && p < P) {
 #pragma unroll
                 for (int w = 0; w < kWarps; ++w) {
-                    const uint32_t cnt = wcnt[w * D + d];
-                    wcnt[w * D + d] = (uint16_t)sum;
-                    sum += cnt;
+                    const uint32_t v = wc32[w * P + p];
+                    wc32[w * P + p] = s0 | (s1 << 16);  // counts of a tile fit 16 bits
+                    s0 += v & 0xffffu;
+                    s1 += v >> 16;
                 }
             }
-            tcount[j] = sum;
-            loc += sum;
-        }
-        {
-            uint32_t x = loc;
+            c0[j] = s0;
+            c1[j] = s1;
+            uint32_t x = s0 + s1;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += t;
             }
-            if (lane == 31) s_scan[warp] = x;
-            __syncthreads();  // S
-            uint32_t tr = x - loc;
+            xs[j] = x - s0 - s1;  // exclusive within the warp
+            if (lane == 31 && j < ppt) s_scan[j * kWarps + warp] = x;
+        }
+        __syncthreads();  // S
+        uint32_t nranked;  // the tile's ranked elements (dropped ones are not)
+        {
+            const int ncol = ppt * kWarps;  // <= 32
+            const uint32_t v = lane < ncol ? s_scan[lane] : 0u;
+            uint32_t x = v;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                tr += (w < warp) ? s_scan[w] : 0u;
-                nranked += s_scan[w];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
             }
+            nranked = __shfl_sync(0xffffffffu, x, 31);
+            x -= v;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int d = dlo + j;
-                if (d < dhi) {
-                    tstart[d] = tr;
-                    dglob[d] = run[d] - tr;
-                    run[d] += tcount[j];
-                    tr += tcount[j];
+            for (int j = 0; j < kScatterCols; ++j) {
+                const uint32_t base = __shfl_sync(0xffffffffu, x, (j * kWarps + warp) & 31);
+                const int p = tid + j * kThreads;
+                if (j < ppt && p < P) {
+                    const uint32_t t0 = base + xs[j], t1 = t0 + c0[j];
+                    uint2 rr = run2[p];
+                    tstart2[p] = make_uint2(t0, t1);
+                    dglob2[p] = make_uint2(rr.x - t0, rr.y - t1);
+                    rr.x += c0[j];
+                    rr.y += c1[j];
+                    run2[p] = rr;
                 }
             }
         }
