@@ -1065,8 +1065,22 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(const __grid_constant__ Ct
     const int tile = sg.scan_tile, ipt = tile / kThreads;  // 1, 2, 4 or 8 rows per thread
     const int64_t n0 = (int64_t)t * tile;
     const int n = (int)min64(tile, (int64_t)sg.N - n0);
+    const int sb = sg.npass == 2 ? sg.lbits : 0;
+    const uint32_t *bucket = sg.npass == 2 ? sg.cnt2 : sg.cnt1;
+    // every global read of the thread's rows is issued first (the bucket bases and labels
+    // do not depend on the scan, the class sizes only on the labels)
+    uint32_t base[kScanItems];
+    int yv[kScanItems], ny[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = tid + k * kThreads;
+        base[k] = (i < n && sg.E > 0) ? __ldcg(bucket + ((n0 + i) >> sb)) : 0u;
+        yv[k] = (i < n && !sg.wdeg) ? __ldg(sg.y + n0 + i) : -1;
+    }
     auto pad = [](int i) { return i + (i >> 5); };
     for (int i = tid; i < tile; i += kThreads) buf[pad(i)] = (i < n) ? __ldcg(sg.rowcnt + n0 + i) : 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldcg(sg.nk + yv[k]) : 0;
     __syncthreads();
     uint32_t loc = 0;
 #pragma unroll
@@ -1085,22 +1099,9 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(const __grid_constant__ Ct
     }
     __syncthreads();
     uint32_t err = 0;
-    const int sb = sg.npass == 2 ? sg.lbits : 0;
     const int gmask = (1 << sb) - 1;  // row offset within its group
-    const uint32_t *bucket = sg.npass == 2 ? sg.cnt2 : sg.cnt1;
     const bool lap = (sg.flags & kOptLap) != 0;
     const float aug = (sg.flags & kOptAug) ? 1.0f : 0.0f;
-    // every global read of the thread's rows first (one round trip each), then the writes
-    uint32_t base[kScanItems];
-    int yv[kScanItems], ny[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int i = tid + k * kThreads;
-        base[k] = (i < n && sg.E > 0) ? __ldcg(bucket + ((n0 + i) >> sb)) : 0u;
-        yv[k] = (i < n && !sg.wdeg) ? __ldg(sg.y + n0 + i) : -1;
-    }
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldcg(sg.nk + yv[k]) : 0;
     const bool buckets = sg.K > kRegK;
     int bks[kScanItems];       // K > 8: length bucket of each light row of this thread (-1: none)
     uint32_t rk[kScanItems];   // its rank among this CTA's rows of that bucket
@@ -2030,6 +2031,9 @@ __global__ void __launch_bounds__(kThreads, SpmmOcc<V>::kMinBlocks) k_spmm(const
 // empties the hub and bucket work so that k_spmm only reads in-range memory.  k_nodetab
 // then rebuilds the node table s_j = D_jj^-1/2 / n_{y_j} from the stored D^-1/2.
 
+constexpr int kRelabelItems = 4;                          // nodes per thread
+constexpr int kRelabelTile = kRelabelItems * kThreads;    // nodes per CTA
+
 __global__ void __launch_bounds__(kThreads) k_labels(const __grid_constant__ Ctx c) {
     __shared__ uint32_t h[kMaxK];
     __shared__ uint32_t s_err;
@@ -2044,14 +2048,20 @@ __global__ void __launch_bounds__(kThreads) k_labels(const __grid_constant__ Ctx
         }
     }
     for (int i = tid; i < g.K; i += kThreads) h[i] = 0;
+    // tiles of kRelabelTile nodes; every label read of the thread is in flight at once
+    const int64_t n0 = (int64_t)blockIdx.x * kRelabelTile;
+    int yv[kRelabelItems];
+#pragma unroll
+    for (int q = 0; q < kRelabelItems; ++q) {
+        const int64_t j = n0 + tid + q * kThreads;
+        yv[q] = j < g.N ? __ldg(g.y + j) : -1;
+    }
     __syncthreads();
-    const int64_t n0 = (int64_t)blockIdx.x * kPrepTile;
-    const int n = (int)min64(kPrepTile, (int64_t)g.N - n0);
     uint32_t err = 0;
-    for (int i = tid; i < n; i += kThreads) {
-        const int yv = __ldg(g.y + n0 + i);
-        if (yv < -1 || yv >= g.K) err |= kStLabel;
-        else if (yv >= 0) atomicAdd(&h[yv], 1u);
+#pragma unroll
+    for (int q = 0; q < kRelabelItems; ++q) {
+        if (yv[q] < -1 || yv[q] >= g.K) err |= kStLabel;
+        else if (yv[q] >= 0) atomicAdd(&h[yv[q]], 1u);
     }
     if (err) atomicOr(&s_err, err);
     __syncthreads();
@@ -2060,17 +2070,29 @@ __global__ void __launch_bounds__(kThreads) k_labels(const __grid_constant__ Ctx
     if (tid == 0 && s_err) atomicOr(g.status, s_err);
 }
 
+// Node table with the new labels: kRelabelItems nodes per thread, their label and degree
+// reads in flight at once, then their class sizes.
 __global__ void __launch_bounds__(kThreads) k_nodetab(const __grid_constant__ Ctx c) {
     const GraphDesc &g = c.g0;
     const bool lap = (g.flags & kOptLap) != 0;
-    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < g.N; j += (int64_t)gridDim.x * kThreads) {
-        const int yv = __ldg(g.y + j);
+    const int64_t n0 = (int64_t)blockIdx.x * kRelabelTile + threadIdx.x;
+    int yv[kRelabelItems], ny[kRelabelItems];
+    float dv[kRelabelItems];
+#pragma unroll
+    for (int q = 0; q < kRelabelItems; ++q) {
+        const int64_t j = n0 + q * kThreads;
+        yv[q] = j < g.N ? __ldg(g.y + j) : -1;
+        dv[q] = (lap && j < g.N) ? __ldcg(g.dinv + j) : 1.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < kRelabelItems; ++q) ny[q] = (yv[q] >= 0 && yv[q] < g.K) ? __ldcg(g.nk + yv[q]) : 0;
+#pragma unroll
+    for (int q = 0; q < kRelabelItems; ++q) {
+        const int64_t j = n0 + q * kThreads;
+        if (j >= g.N) continue;
         int2 tv = make_int2(0, 0);
-        if (yv >= 0 && yv < g.K) {
-            const int ny = __ldcg(g.nk + yv);
-            const float dv = lap ? __ldcg(g.dinv + j) : 1.0f;
-            tv = make_int2(yv, __float_as_int(ny > 0 ? dv / (float)ny : 0.0f));
-        }
+        if (yv[q] >= 0 && yv[q] < g.K)
+            tv = make_int2(yv[q], __float_as_int(ny[q] > 0 ? dv[q] / (float)ny[q] : 0.0f));
         g.tab[j] = tv;
     }
 }
@@ -2100,10 +2122,11 @@ cudaError_t launch_nodetab(const Ctx &c, cudaStream_t st) {
 cudaError_t launch_relabel(const Ctx &c, cudaStream_t st) {
     const int64_t N = c.g0.N;
     if (N <= 0) return cudaSuccess;
-    k_labels<<<(int)((N + kPrepTile - 1) / kPrepTile), kThreads, 0, st>>>(c);
+    const int tiles = (int)((N + kRelabelTile - 1) / kRelabelTile);
+    k_labels<<<tiles, kThreads, 0, st>>>(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_nodetab<<<(int)min64((N + kThreads - 1) / kThreads, 152 * 8), kThreads, 0, st>>>(c);
+    k_nodetab<<<tiles, kThreads, 0, st>>>(c);
     return cudaGetLastError();
 }
 
