@@ -982,7 +982,9 @@ __device__ __forceinline__ void write_node_known(const GraphDesc &g, int64_t j, 
 
 __device__ __forceinline__ void write_node(const GraphDesc &g, int64_t j, float deg, bool lap) {
     const int yv = __ldg(g.y + j);
-    const int ny = (yv >= 0 && yv < g.K) ? __ldcg(g.nk + yv) : 0;
+    // n_k is final before any kernel that reads it here: the read-only path lets L1 take
+    // the repeated reads of the few class sizes that every node asks for
+    const int ny = (yv >= 0 && yv < g.K) ? __ldg(g.nk + yv) : 0;
     write_node_known(g, j, deg, lap, yv, ny);
 }
 
@@ -1080,7 +1082,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(const __grid_constant__ Ct
     auto pad = [](int i) { return i + (i >> 5); };
     for (int i = tid; i < tile; i += kThreads) buf[pad(i)] = (i < n) ? __ldcg(sg.rowcnt + n0 + i) : 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldcg(sg.nk + yv[k]) : 0;
+    for (int k = 0; k < kScanItems; ++k) ny[k] = (yv[k] >= 0 && yv[k] < sg.K) ? __ldg(sg.nk + yv[k]) : 0;  // through L1
     __syncthreads();
     uint32_t loc = 0;
 #pragma unroll
@@ -1292,7 +1294,7 @@ __device__ __forceinline__ uint32_t load_block_rows(const GraphDesc &g, int64_t 
         br.rs = min(max(a, 0), E32);
         br.re = min(max(b, br.rs), E32);
     }
-    if (!SPMM && br.y >= 0 && br.y < g.K) br.ny = __ldcg(g.nk + br.y);
+    if (!SPMM && br.y >= 0 && br.y < g.K) br.ny = __ldg(g.nk + br.y);  // final n_k, through L1
     uint32_t key = kNoRow;
     const int len = br.re - br.rs;
     is_short = has && len <= short_len;
@@ -2085,7 +2087,7 @@ __global__ void __launch_bounds__(kThreads) k_nodetab(const __grid_constant__ Ct
         dv[q] = (lap && j < g.N) ? __ldcg(g.dinv + j) : 1.0f;
     }
 #pragma unroll
-    for (int q = 0; q < kRelabelItems; ++q) ny[q] = (yv[q] >= 0 && yv[q] < g.K) ? __ldcg(g.nk + yv[q]) : 0;
+    for (int q = 0; q < kRelabelItems; ++q) ny[q] = (yv[q] >= 0 && yv[q] < g.K) ? __ldg(g.nk + yv[q]) : 0;  // through L1
 #pragma unroll
     for (int q = 0; q < kRelabelItems; ++q) {
         const int64_t j = n0 + q * kThreads;
